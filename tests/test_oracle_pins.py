@@ -1,0 +1,318 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix, independently
+of the oracle's own code: closed forms, limits of the kernel bandwidth, exact
+reconstruction of signals the estimators must reproduce, invariances, brute force on
+tiny inputs, and the values Table I prints."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_11226_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def isolated(frame, by=7, bx=7):
+    m = np.zeros(((frame.shape[0] + 15) // 16, (frame.shape[1] + 15) // 16), np.uint8)
+    m[by, bx] = 1
+    return m
+
+
+def region_avail_first_step(frame, by=7, bx=7):
+    """Availability of the 48x48 support region of an isolated lost block before any
+    patch is filled (Sec. II: the 8 neighbours are support, the block itself is not)."""
+    A = np.ones((48, 48), bool)
+    A[16:32, 16:32] = False
+    oy, ox = by * 16 - 16, bx * 16 - 16
+    R = frame[oy:oy + 48, ox:ox + 48].astype(np.float64)
+    return R, A
+
+
+def brute_candidates(A, cfg):
+    """All window positions (u, v) whose configured positions are all available."""
+    out = []
+    for u in range(43):
+        for v in range(43):
+            if all(A[u + r, v + c] for r, c in cfg):
+                out.append((u, v))
+    return out
+
+
+# ---------------------------------------------------------------------------------------
+# Table I / Sec. IV-B constants
+
+def test_table1_profiles_golden():
+    rows = {}
+    for line in open(os.path.join(GOLDEN, "table1_profiles.txt")):
+        line = line.split("#")[0].split()
+        if line:
+            rows[line[0]] = [float(v) for v in line[1:]]
+    for name in ("express", "efficient", "excellent"):
+        p = oracle.params(name)
+        assert (p.t_phi, p.t_nu) == tuple(rows[name])
+        assert p.sigma2 == rows["sigma2"][0]
+
+
+# ---------------------------------------------------------------------------------------
+# whole-method invariants
+
+@pytest.mark.parametrize("mode", ["efficient", "force_idl", "force_hql"])
+def test_constant_frame_conceals_to_constant(mode):
+    f = np.full((64, 64), 137, np.uint8)
+    m = np.zeros((4, 4), np.uint8)
+    m[1, 1] = m[2, 2] = m[1, 2] = 1
+    kw = {}
+    if mode == "force_idl":
+        kw = dict(t_phi=-1.0, t_nu=1e-300)
+    elif mode == "force_hql":
+        kw = dict(t_phi=-1.0, t_nu=1e300)
+    r = oracle.conceal(f, m, oracle.params("efficient", **kw))
+    assert np.all(np.abs(r["out"] - 137.0) < 1e-9)
+
+
+def test_received_unchanged_lost_inputs_ignored():
+    f, m = synth.workload_checkerboard(3, 96, 96)
+    r1 = oracle.conceal(f, m)
+    g = f.copy()
+    lost = synth.lost_pixel_mask(m, 96, 96)
+    g[lost] = np.random.default_rng(0).integers(0, 256, size=lost.sum())
+    r2 = oracle.conceal(g, m)
+    assert np.array_equal(r1["out"], r2["out"])
+    assert np.array_equal(r1["out"][~lost], f[~lost].astype(np.float64))
+
+
+def test_shift_equivariance():
+    f = synth.make_frame(128, 128, 11)
+    f = (30 + (f.astype(np.int32) * 170) // 255).astype(np.uint8)  # [30, 200]
+    m = synth.loss_checkerboard(128, 128)
+    m[2, 2] = 1  # one chained block too
+    a = oracle.conceal(f, m, oracle.params("efficient"), trace=True)
+    b = oracle.conceal((f + 40).astype(np.uint8), m, oracle.params("efficient"), trace=True)
+    lost = synth.lost_pixel_mask(m, 128, 128)
+    assert np.max(np.abs(b["out"][lost] - a["out"][lost] - 40.0)) < 1e-6
+    assert np.array_equal(a["trace"]["layer"], b["trace"]["layer"])
+
+
+def test_affine_equivariance_hql():
+    # HQL only: Mahalanobis distances, beta and alpha are invariant to I -> s*I + c
+    # (8-bit inputs: an even-valued frame f and f/2 + 60 are both exact)
+    # (values kept in [64, 192] so that no estimate reaches the clipping bounds)
+    f = synth.make_frame(96, 96, 5).astype(np.int32)
+    f = (64 + (f * 128 // 255) // 2 * 2).astype(np.uint8)
+    m = isolated(f, 2, 2)
+    # The ridge's absolute 1e-6 floor does not scale, so a near-tie of I0 or beta* may
+    # resolve differently; values must agree step by step up to the first such decision.
+    p = oracle.params("efficient", t_phi=-1.0, t_nu=1e300)
+    ta = oracle.conceal(f, m, p, trace=True)["trace"][0]
+    tb = oracle.conceal((f // 2 + 60).astype(np.uint8), m, p, trace=True)["trace"][0]
+    n = 0
+    for a, b in zip(ta, tb):
+        if a["beta_idx"] != b["beta_idx"] or not np.array_equal(a["i0"], b["i0"]):
+            assert min(a["margin_i0"], a["margin_beta"]) < 1e-3
+            break
+        assert a["patch"] == b["patch"]
+        assert np.max(np.abs(b["x"] - (0.5 * a["x"] + 60.0))) < 1e-4
+        assert abs(a["alpha"] - b["alpha"]) < 1e-4
+        n += 1
+    assert n >= 16
+
+
+def test_fully_lost_frame_fills_128():
+    f = synth.make_frame(48, 48, 1)
+    m = np.ones((3, 3), np.uint8)
+    r = oracle.conceal(f, m, trace=True)
+    assert np.all(r["out"] == 128.0)
+    assert r["trace"][0, 0]["layer"] == oracle.EMPTY
+
+
+def test_threads_and_sampling_are_exact():
+    f, m = synth.workload_slice_1080p(2)
+    f, m = f[:256, :320].copy(), m[:16, :20].copy()
+    a = oracle.conceal(f, m, threads=1)["out"]
+    b = oracle.conceal(f, m, threads=4)["out"]
+    assert np.array_equal(a, b)
+    sel = np.zeros_like(m)
+    ys, xs = np.nonzero(m)
+    sel[ys[-1], xs[-1]] = 1  # last lost block: needs its whole ancestor chain
+    c = oracle.conceal(f, m, select=sel)["out"]
+    blk = (slice(ys[-1] * 16, ys[-1] * 16 + 16), slice(xs[-1] * 16, xs[-1] * 16 + 16))
+    assert np.array_equal(c[blk], a[blk])
+
+
+def test_rejects_odd_sizes():
+    with pytest.raises(ValueError):
+        oracle.conceal(np.zeros((33, 32), np.uint8), np.ones((3, 2), np.uint8))
+
+
+# ---------------------------------------------------------------------------------------
+# fill order (Sec. II, Fig. 1(b) caption: outer border towards the centre)
+
+def test_fill_order_starts_at_the_border():
+    # R2 (count of available context pixels, ties to the lowest index): the four corners,
+    # whose windows see 20 received pixels, come first; every patch is filled once; every
+    # patch touches available context when it is filled; the centre patches come last.
+    f = synth.make_frame(128, 128, 4)
+    r = oracle.conceal(f, isolated(f, 3, 3), trace=True)
+    t = r["trace"][0]
+    order = list(t["patch"])
+    assert sorted(order) == list(range(64))
+    assert order[:4] == [0, 7, 56, 63]
+    assert list(t["ny"][:4]) == [20, 20, 20, 20]
+    assert (t["ny"] >= 12).all()
+    ring_of = lambda p: min(p // 8, p % 8, 7 - p // 8, 7 - p % 8)
+    assert ring_of(order[-1]) <= 3 and all(ring_of(p) == 0 for p in order[:4])
+
+
+# ---------------------------------------------------------------------------------------
+# BRL, Eq. (16): mean of the context
+
+def test_brl_first_patch_is_context_mean():
+    rng = np.random.default_rng(7)
+    f = rng.integers(100, 116, size=(128, 128)).astype(np.uint8)  # phi <= 15 < 20 everywhere
+    r = oracle.conceal(f, isolated(f, 3, 3), trace=True)
+    R, A = region_avail_first_step(f, 3, 3)
+    win = R[14:20, 14:20][A[14:20, 14:20]]  # window of patch (0,0)
+    t0 = r["trace"][0, 0]
+    assert t0["layer"] == oracle.BRL and t0["patch"] == 0 and t0["ny"] == 20
+    assert abs(t0["x"][0] - win.mean()) < 1e-12
+    assert abs(r["out"][48, 48] - win.mean()) < 1e-12
+
+
+def test_no_candidate_falls_back_to_brl():
+    # 18x16 frame: the only support of the lost block is a 2-row strip, too thin for any
+    # candidate (x rows plus context rows need 4 available rows)
+    f = synth.make_frame(16, 18, 9)
+    m = np.array([[1], [0]], np.uint8)
+    r = oracle.conceal(f, m, oracle.params("efficient", t_phi=-1.0), trace=True)
+    t0 = r["trace"][0, 0]
+    assert t0["layer"] == oracle.BRL_NOCAND and t0["m"] == 0
+    # patch (7,1): rows 14-15, cols 2-3; context = available rows 16-17, cols 0-5
+    assert t0["patch"] == 57
+    assert abs(t0["x"][0] - f[16:18, 0:6].mean()) < 1e-12
+
+
+# ---------------------------------------------------------------------------------------
+# IDL, Eq. (15): limits of the aperture sigma^2
+
+def periodic_frame(py=3, px=4, seed=0, size=128):
+    rng = np.random.default_rng(seed)
+    tile = rng.integers(20, 236, size=(py, px))
+    yy, xx = np.mgrid[0:size, 0:size]
+    return tile[yy % py, xx % px].astype(np.uint8)
+
+
+def test_idl_sigma_to_zero_reconstructs_periodic_texture_exactly():
+    # sigma^2 -> 0: only exact context matches keep weight, so a periodic texture whose
+    # period fits in the first ring is reconstructed exactly, patch after patch
+    f = periodic_frame()
+    m = isolated(f, 3, 3)
+    p = oracle.params("efficient", t_phi=-1.0, t_nu=0.5, sigma2=1e-9)
+    r = oracle.conceal(f, m, p, trace=True)
+    assert (r["trace"][0]["layer"] == oracle.IDL).all()
+    lost = synth.lost_pixel_mask(m, 128, 128)
+    assert np.array_equal(r["out"][lost], f[lost].astype(np.float64))
+
+
+def test_idl_sigma_to_infinity_is_plain_candidate_mean():
+    f = synth.make_frame(128, 128, 21)
+    m = isolated(f, 3, 3)
+    p = oracle.params("efficient", t_phi=-1.0, t_nu=0.5, sigma2=1e15)
+    r = oracle.conceal(f, m, p, trace=True)
+    t0 = r["trace"][0, 0]
+    assert t0["layer"] == oracle.IDL and t0["ring"] == 1 and t0["patch"] == 0
+    R, A = region_avail_first_step(f, 3, 3)
+    cfg = [(rr, cc) for rr in range(6) for cc in range(6) if A[14 + rr, 14 + cc]]
+    cfg += [(2, 2), (2, 3), (3, 2), (3, 3)]
+    cands = [(u, v) for (u, v) in brute_candidates(A, cfg)
+             if max(abs(u + 2 - 16), abs(v + 2 - 16)) <= 4]
+    xs = np.array([[R[u + 2, v + 2], R[u + 2, v + 3], R[u + 3, v + 2], R[u + 3, v + 3]]
+                   for u, v in cands])
+    assert np.max(np.abs(t0["x"] - xs.mean(0))) < 1e-6
+
+
+def test_nu_bounded_by_candidate_count():
+    f, m = synth.workload_checkerboard(5, 160, 160)
+    r = oracle.conceal(f, m, oracle.params("excellent"), trace=True)
+    t = r["trace"].reshape(-1)
+    sel = (t["layer"] == oracle.IDL) | (t["layer"] == oracle.HQL)
+    assert sel.any()
+    # nu is a sum of at most M raw weights, each <= 1 (R6: the exponent is non-positive)
+    assert np.all(t["log_nu"][sel] <= np.log(np.maximum(t["m"][sel], 1)) + 1e-12)
+
+
+# ---------------------------------------------------------------------------------------
+# HQL, Eq. (13)
+
+def test_hql_reconstructs_linear_signal_exactly():
+    # candidates of an exactly linear (in the pixel values) image satisfy z_j = z_0 + t_j 1;
+    # then C_XY C_YY^-1 maps the context residual to the patch exactly, every leave-one-out
+    # residual equals its correction (alpha* >= 1, clamped to 1) and Eq. (13) returns the
+    # true patch up to the 1e-6 ridge floor.
+    yy, xx = np.mgrid[0:112, 0:112]
+    f = (yy + xx + 10).astype(np.uint8)
+    m = isolated(f, 3, 3)
+    p = oracle.params("efficient", t_phi=-1.0, t_nu=1e300, ridge_rel=0.0)
+    r = oracle.conceal(f, m, p, trace=True)
+    assert (r["trace"][0]["layer"] == oracle.HQL).all()
+    lost = synth.lost_pixel_mask(m, 112, 112)
+    assert np.max(np.abs(r["out"][lost] - f[lost])) < 1e-4
+    assert np.all(r["trace"][0]["alpha"] > 1.0 - 1e-6)
+
+
+def numpy_hql(R, A, pr, pc, p):
+    """Independent NumPy statement of one HQL estimate (Eqs. (3)-(13), readings R5/R7)
+    for the patch with top-left (pr, pc) of a 48x48 region R with availability A."""
+    wr, wc = pr - 2, pc - 2
+    cfg = [(r, c) for r in range(6) for c in range(6) if A[wr + r, wc + c]]
+    y0 = np.array([R[wr + r, wc + c] for r, c in cfg])
+    xcfg = [(2, 2), (2, 3), (3, 2), (3, 3)]
+    cands = brute_candidates(A, cfg + xcfg)
+    X = np.array([[R[u + r, v + c] for r, c in xcfg] for u, v in cands])
+    Y = np.array([[R[u + r, v + c] for r, c in cfg] for u, v in cands])
+    Zm = np.hstack([X, Y])
+    C = np.cov(Zm, rowvar=False, bias=True)
+    ny = len(cfg)
+    Cyy = C[4:, 4:] + (p.ridge_rel * np.trace(C[4:, 4:]) / ny + 1e-6) * np.eye(ny)
+    Cxy = C[:4, 4:]
+    P = np.linalg.inv(Cyy)
+    K = np.linalg.solve(Cyy, Cxy.T).T
+    d = np.einsum("ij,jk,ik->i", Y - y0, P, Y - y0)
+    betas = 2.0 ** (0.5 * np.arange(p.beta_kmin, p.beta_kmax + 1))
+    def w_of(dd, beta):
+        w = np.exp(-(dd - dd.min()) / (2 * beta))
+        return w / w.sum()
+    eps = np.array([np.sum((y0 - w_of(d, b) @ Y) ** 2) for b in betas])
+    bi = int(np.flatnonzero(eps <= eps.min() * (1 + p.beta_tie_rel))[0])
+    w = w_of(d, betas[bi])
+    xt, yt = w @ X, w @ Y
+    n0 = min(ny + 1, len(cands) - 1)
+    I0 = np.lexsort((np.arange(len(d)), d))[:n0]
+    R_, G_ = [], []
+    for i in I0:
+        di = np.einsum("ij,jk,ik->i", Y - Y[i], P, Y - Y[i])
+        mask = np.arange(len(d)) != i
+        wi = w_of(di[mask], betas[bi])
+        R_.append(X[i] - wi @ X[mask])
+        G_.append(K @ (Y[i] - wi @ Y[mask]))
+    R_, G_ = np.array(R_), np.array(G_)
+    alphas = np.linspace(-0.5, 1.5, 20001)
+    epsx = [np.mean(np.sum((R_ - a * G_) ** 2, axis=1)) for a in alphas]
+    a_scan = float(np.clip(alphas[int(np.argmin(epsx))], 0, 1))
+    a_cf = float(np.clip(np.sum(R_ * G_) / np.sum(G_ * G_), 0, 1))
+    return xt + a_cf * K @ (y0 - yt), a_cf, a_scan, bi, len(cands)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_hql_first_patch_matches_numpy_brute_force(seed):
+    f = synth.make_frame(128, 128, seed)
+    m = isolated(f, 3, 3)
+    p = oracle.params("efficient", t_phi=-1.0, t_nu=1e300)
+    r = oracle.conceal(f, m, p, trace=True)
+    t0 = r["trace"][0, 0]
+    R, A = region_avail_first_step(f, 3, 3)
+    xhat, a_cf, a_scan, bi, M = numpy_hql(R, A, 16, 16, p)
+    assert t0["layer"] == oracle.HQL and t0["m"] == M and t0["beta_idx"] == bi
+    assert abs(a_cf - t0["alpha"]) < 1e-9
+    assert abs(a_scan - a_cf) <= 1e-4  # the closed form is the minimiser of Eq. (11)
+    assert np.max(np.abs(np.clip(xhat, 0, 255) - t0["x"])) < 1e-8

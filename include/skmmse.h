@@ -1,0 +1,195 @@
+/*
+ * skmmse.h -- C ABI of the GB300 (sm_103a) implementation of scalable kernel-based
+ * MMSE (SK-MMSE) spatial error concealment, Koloda, Seiler, Peinado, Kaup,
+ * arXiv 2205.11226.
+ *
+ * Problem statement (Sec. II): a frame R = L u S holds missing pixels L (here: whole
+ * 16x16 blocks flagged in a block-loss map) and available pixels S.  Each lost block is
+ * filled 2x2 patch by 2x2 patch from its border inwards; every patch x0 is estimated
+ * from its context y0 (the available pixels of the 6x6 window centred on x0) and from
+ * candidates z_j = (x_j, y_j) with the same spatial configuration found in the 8
+ * neighbouring blocks, by one of three layers chosen per patch by a profile (Sec. V):
+ *   BRL  context mean, Eq. (16), when the flatness phi = max(y0) - min(y0) <= T_phi
+ *        (Eq. (17));
+ *   IDL  exponential weights with scalar bandwidth sigma^2 * Ny over a support area
+ *        growing from x0, Eq. (15), accepted when the normaliser nu >= T_nu (Eq. (18));
+ *   HQL  full K-MMSE with sample-covariance bandwidth and beta/alpha fitting,
+ *        Eq. (13) with Eqs. (3)-(12).
+ * A reconstructed patch joins the support (end of Sec. III).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* and the pointers inside skmmse_frame are DEVICE memory owned by
+ *     the caller; h_* pointers are host memory owned by the caller.  The library never
+ *     frees caller memory.
+ *   - Frames are 8-bit luma, `height` rows of `pitch` bytes; width and height must be
+ *     even and positive.  The block-loss map has ceil(height/16) rows of ceil(width/16)
+ *     bytes, non-zero = lost.  Partial blocks at the right/bottom edge conceal only their
+ *     in-frame pixels.  Input values of lost pixels are never read.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream).  Argument errors are returned synchronously and enqueue nothing; device
+ *     errors (a dependency wait that gave up) are reported by skmmse_read_stats().
+ *     Passing a non-NULL h_stats makes the call synchronous on `stream`.
+ *   - A context owns device scratch memory (work queue, dependency flags, the unrounded
+ *     values of concealed blocks, counters), grown on demand with cudaMalloc and freed by
+ *     skmmse_destroy().  Calls sharing a context must be ordered on one stream; use one
+ *     context per concurrently running stream.
+ *   - No exception crosses this ABI.  All functions are thread-compatible, not
+ *     thread-safe on one context.
+ */
+#ifndef SKMMSE_H_
+#define SKMMSE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SKMMSE_ABI_VERSION 1
+
+typedef enum {
+    SKMMSE_OK = 0,
+    SKMMSE_ERR_ARG = 1,         /* NULL pointer, bad parameter value */
+    SKMMSE_ERR_SHAPE = 2,       /* odd or non-positive size, pitch < width, too many frames */
+    SKMMSE_ERR_ALIGN = 3,       /* pointer or pitch alignment not supported */
+    SKMMSE_ERR_NOMEM = 4,       /* scratch allocation failed */
+    SKMMSE_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+    SKMMSE_ERR_TIMEOUT = 6,     /* a block's dependency wait gave up (device error word) */
+    SKMMSE_ERR_UNSUPPORTED = 7  /* requested precision or flag not built */
+} skmmse_status;
+
+/* Arithmetic of the distance contraction.  FP32: every step in FP32 on the CUDA cores
+   (HQL covariance and Cholesky with exact/compensated FP32 arithmetic).  The mixed modes
+   run the template-distance contractions on tcgen05 tensor cores. */
+typedef enum { SKMMSE_FP32 = 0, SKMMSE_MIXED_BF16 = 1, SKMMSE_MIXED_FP16 = 2 } skmmse_precision;
+
+/* Profiles of Table I (T_phi, T_nu): express (20, 0.01), efficient (20, 0.1),
+   excellent (20, 100). */
+typedef enum { SKMMSE_EXPRESS = 0, SKMMSE_EFFICIENT = 1, SKMMSE_EXCELLENT = 2 } skmmse_profile;
+
+/* flags */
+#define SKMMSE_FLAG_TRACE 1u   /* write per-patch decision records (skmmse_frame.trace) */
+/* Verification hook (requires SKMMSE_FLAG_TRACE): the trace buffer is read before it is
+   written; its x[4] fields hold reference estimates, which the kernel writes back into
+   the support instead of its own estimates ("teacher forcing").  The records written
+   carry the kernel's own estimates, so each step can be compared with a reference on
+   identical inputs.  Outputs then hold the reference values.  Not for production use. */
+#define SKMMSE_FLAG_FORCE 2u
+
+typedef struct {
+    float t_phi;        /* flatness threshold T_phi, Eq. (17) / Table I; BRL iff phi <= T_phi */
+    float t_nu;         /* normalisation threshold T_nu, Eq. (18) / Table I; must be > 0 */
+    float sigma2;       /* IDL aperture sigma^2, Eq. (14); 10 in the paper (Sec. IV-B) */
+    int ring_step;      /* IDL support growth: ring k holds candidate patches at Chebyshev
+                           distance in ((k-1)*ring_step, k*ring_step] from x0; >= 1 */
+    float ridge_rel;    /* HQL: C_YY += (ridge_rel * trace(C_YY)/Ny + 1e-6) I; >= 0 */
+    int beta_kmin;      /* HQL beta grid: beta = 2^(k/2), k = beta_kmin..beta_kmax */
+    int beta_kmax;      /*   (at most 32 grid values) */
+    float beta_tie_rel; /* HQL: beta* = smallest grid beta with eps_y <= (1+tie) min eps_y */
+    int concealed_is_support; /* 1: blocks concealed earlier in raster order are support */
+    int precision;      /* skmmse_precision */
+    unsigned flags;     /* SKMMSE_FLAG_* */
+} skmmse_params;
+
+/* One frame of a batch.  All pointers are device memory.  `out` may equal `frame`
+   (in-place).  `out_f32` (nullable) receives unrounded values: every pixel of a lost
+   block in the frame; received pixels are not written.  `trace` (nullable, used with
+   SKMMSE_FLAG_TRACE) holds n_lost*64 skmmse_trace_rec, indexed by
+   [rank of the block among the frame's lost blocks in raster order][fill step]. */
+typedef struct {
+    const uint8_t* frame;
+    int width, height, pitch;
+    const uint8_t* mb_lost;
+    uint8_t* out;
+    int out_pitch;
+    float* out_f32;
+    int out_f32_pitch;  /* in floats */
+    void* trace;
+} skmmse_frame;
+
+/* Per-patch decision record (SKMMSE_FLAG_TRACE). */
+typedef struct {
+    int32_t mb;         /* block raster index in its frame */
+    int16_t step;       /* fill step inside the block */
+    int16_t patch;      /* patch index a*8+b (a = patch row, b = patch column) */
+    int8_t layer;       /* 0 Ny=0 fill, 1 BRL, 2 IDL, 3 HQL, 4 BRL (no candidate) */
+    int8_t ring;        /* IDL: accepted ring; otherwise rings evaluated */
+    int8_t beta_idx;    /* HQL: index of beta* in the grid, else -1 */
+    int8_t n0;          /* HQL: |I0| */
+    int16_t ny;         /* context size */
+    int16_t m;          /* candidates in the whole support (when enumerated) */
+    float phi;          /* flatness */
+    float log_nu;       /* log nu after the last ring evaluated */
+    float alpha;        /* HQL alpha after clamping */
+    float eps_best;     /* HQL eps_y(beta*) */
+    float x[4];         /* estimate after clipping */
+    uint16_t i0[36];    /* HQL I0 as window indices wu*43+wv (43 positions per axis in the
+                           48x48 support region), ascending; unused entries 0xffff */
+} skmmse_trace_rec;
+
+/* Counters of one call (summed over the batch). */
+typedef struct {
+    long long n_lost_mbs;
+    long long n_patches, n_empty, n_brl, n_idl, n_hql, n_brl_nocand;
+    long long idl_ring_hist[16];
+    long long idl_cand_evals;   /* IDL candidate distance evaluations */
+    long long idl_ny_evals;     /* sum of Ny over those evaluations */
+    long long hql_cands;        /* sum of M over HQL patches */
+    long long hql_ny_cands;     /* sum of M*Ny over HQL patches */
+    long long hql_i0_cands;     /* sum of |I0|*M over HQL patches */
+    long long alg_flops;        /* algorithmic FP32 operations of the call (per-layer formulas
+                                   of the design document; an exp counts as one) */
+    long long n_beta;           /* beta grid size of the call */
+    int error;                  /* 0, or SKMMSE_ERR_TIMEOUT */
+    int pad;
+} skmmse_stats;
+
+typedef struct skmmse_context skmmse_context;
+
+/* Library and ABI version (SKMMSE_ABI_VERSION). */
+int skmmse_abi_version(void);
+
+/* Size in bytes of skmmse_trace_rec / skmmse_stats / skmmse_params / skmmse_frame
+   (lets a binding check its struct layout). */
+int skmmse_struct_size(int which /* 0 trace, 1 stats, 2 params, 3 frame */);
+
+/* Human-readable status. Never NULL. */
+const char* skmmse_status_str(skmmse_status s);
+
+/* Fill *p with a Table I profile, sigma^2 = 10 and the default readings of the
+   unstated parts: ring_step 4, ridge_rel 1e-3, beta grid k = -8..16, beta_tie_rel 1e-3,
+   concealed_is_support 1, FP32, no flags.  Unknown profile -> efficient. */
+void skmmse_params_preset(skmmse_params* p, int profile);
+
+/* Create a context on the current CUDA device.  Returns SKMMSE_ERR_ARG for ctx == NULL,
+   SKMMSE_ERR_CUDA if no device is usable. */
+skmmse_status skmmse_create(skmmse_context** ctx);
+
+/* Release the context's scratch memory (synchronises its last stream). NULL is a no-op. */
+void skmmse_destroy(skmmse_context* ctx);
+
+/* Conceal all lost blocks of one frame: the frame's received pixels are copied to d_out,
+   and each lost block is filled by the layered SK-MMSE estimate (Secs. II-V).
+   d_out_f32 (nullable): unrounded values of lost pixels, pitch = width floats.
+   The rounded output is round-half-even of the clipped estimate. */
+skmmse_status skmmse_conceal(skmmse_context* ctx, const uint8_t* d_frame, int width,
+                             int height, int pitch, const uint8_t* d_mb_lost,
+                             const skmmse_params* p, uint8_t* d_out, int out_pitch,
+                             float* d_out_f32, skmmse_stats* h_stats, void* stream);
+
+/* Conceal n frames of any sizes in one persistent launch (one work queue over all lost
+   blocks of all frames, dependency-ordered).  h_frames is a host array of n descriptors
+   (1 <= n <= 65536). */
+skmmse_status skmmse_conceal_batch(skmmse_context* ctx, const skmmse_frame* h_frames, int n,
+                                   const skmmse_params* p, skmmse_stats* h_stats,
+                                   void* stream);
+
+/* Synchronise `stream` and copy the counters of the context's last call into *h_stats.
+   Returns SKMMSE_ERR_TIMEOUT if a dependency wait gave up during that call. */
+skmmse_status skmmse_read_stats(skmmse_context* ctx, skmmse_stats* h_stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SKMMSE_H_ */

@@ -39,6 +39,7 @@ class Params(ctypes.Structure):
         ("beta_kmax", ctypes.c_int),
         ("beta_tie_rel", ctypes.c_double),
         ("concealed_is_support", ctypes.c_int),
+        ("store_f32", ctypes.c_int),
     ]
 
 
@@ -74,7 +75,8 @@ def params(profile: str = "efficient", **kw) -> Params:
     of the unstated parts (ring width, ridge, beta grid, beta tie tolerance)."""
     t_phi, t_nu = PROFILES[profile]
     p = Params(t_phi=t_phi, t_nu=t_nu, sigma2=10.0, ring_step=4, ridge_rel=1e-3,
-               beta_kmin=-8, beta_kmax=16, beta_tie_rel=1e-3, concealed_is_support=1)
+               beta_kmin=-8, beta_kmax=16, beta_tie_rel=1e-3, concealed_is_support=1,
+               store_f32=0)
     for k, v in kw.items():
         setattr(p, k, v)
     return p

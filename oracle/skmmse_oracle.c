@@ -43,7 +43,8 @@
  *       I0 = the min(Ny+1, M-1) candidates with the smallest Mahalanobis distance to y0
  *       (ties to the lower index); leave-one-out predictions for i in I0; the alpha that
  *       minimises Eq. (11) in closed form, clamped to [0, 1] (0 if undefined).
- *   R8  every estimate is clipped to [0, 255] and written back unrounded.
+ *   R8  every estimate is clipped to [0, 255] and written back unrounded (store_f32:
+ *       rounded to binary32, to give a binary32 path under test identical inputs).
  */
 #include <math.h>
 #include <pthread.h>
@@ -68,6 +69,8 @@ typedef struct {
     int beta_kmin, beta_kmax; /* HQL beta grid (R7) */
     double beta_tie_rel; /* HQL beta tie tolerance (R7) */
     int concealed_is_support; /* R1 */
+    int store_f32;       /* R8 variant: reconstructions are stored rounded to binary32 (the
+                            storage precision of a path under test); arithmetic stays FP64 */
 } oracle_params;
 
 typedef struct {
@@ -251,11 +254,14 @@ static void hql_estimate(oracle_scratch* s, const oracle_params* p, int M, int n
     int bstar = 0;
     for (int b = 0; b < nb; b++)
         if (eps[b] <= emin * (1.0 + p->beta_tie_rel)) { bstar = b; break; }
+    /* distance of the decision to a flip: a grid value before beta* crossing into the
+       tie band, or beta* itself (when it is not the minimiser) leaving it */
     double mb = INFINITY;
     for (int b = 0; b <= bstar; b++) {
-        double r = emin > 0.0 ? eps[b] / emin : (eps[b] > 0.0 ? INFINITY : 1.0);
+        if (emin <= 0.0) break; /* exact zeros: no ambiguity */
+        double r = eps[b] / emin;
+        if (b == bstar && r == 1.0) continue;
         double g = fabs(r - (1.0 + p->beta_tie_rel));
-        if (emin == 0.0 && eps[b] == 0.0) g = INFINITY; /* exact zeros: no ambiguity */
         if (g < mb) mb = g;
     }
     const double beta_s = pow(2.0, 0.5 * (p->beta_kmin + bstar));
@@ -544,6 +550,7 @@ static void conceal_block(oracle_job* job, oracle_scratch* s, int by, int bx) {
         const int fr[4] = {pr, pr, pr + 1, pr + 1}, fc[4] = {pc, pc + 1, pc, pc + 1};
         for (int a = 0; a < 4; a++) {
             xhat[a] = clip255(xhat[a]);
+            if (p->store_f32) xhat[a] = (double)(float)xhat[a];
             s->R[fr[a]][fc[a]] = xhat[a];
             s->A[fr[a]][fc[a]] = 1;
         }

@@ -1,0 +1,356 @@
+// Host side of the C ABI declared in include/skmmse.h: argument validation, the
+// per-context scratch arena, TMA descriptors, queue construction and the launch of the
+// persistent concealment kernel.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "skmmse.h"
+#include "skmmse_kernel.cuh"
+
+using sk::FrameDev;
+using sk::KParams;
+using sk::WorkDev;
+
+static_assert(sizeof(sk::TraceRec) == sizeof(skmmse_trace_rec), "trace layout");
+
+struct skmmse_context {
+    int device = 0;
+    int sm_count = 0;
+    int blocks_per_sm = 0;
+    size_t smem_bytes = 0;
+    // device arena
+    unsigned char* d_arena = nullptr;
+    size_t arena_bytes = 0;
+    // fixed device buffers
+    int* d_counters = nullptr;               // [0] entries, [1] head, [2] error, [3] pad
+    unsigned long long* d_stats = nullptr;   // kNStats
+    // pinned staging for frame descriptors and tensor maps
+    unsigned char* h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    cudaEvent_t stage_done = nullptr;
+    bool stage_pending = false;
+    long long last_nbeta = 0;
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+};
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+skmmse_status cuda_fail(cudaError_t e) {
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? SKMMSE_ERR_NOMEM : SKMMSE_ERR_CUDA;
+}
+
+#define SK_CHECK(call)                               \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+skmmse_status validate_params(const skmmse_params* p) {
+    if (!p) return SKMMSE_ERR_ARG;
+    if (!(p->t_nu > 0.0f) || !(p->sigma2 > 0.0f) || !(p->ridge_rel >= 0.0f) ||
+        !(p->beta_tie_rel >= 0.0f) || !std::isfinite(p->t_phi) || !std::isfinite(p->t_nu))
+        return SKMMSE_ERR_ARG;
+    if (p->ring_step < 1 || p->ring_step > 64) return SKMMSE_ERR_ARG;
+    const int nb = p->beta_kmax - p->beta_kmin + 1;
+    if (nb < 1 || nb > sk::kMaxBeta || p->beta_kmin < -60 || p->beta_kmax > 60) return SKMMSE_ERR_ARG;
+    if (p->precision != SKMMSE_FP32) {
+        if (p->precision == SKMMSE_MIXED_BF16 || p->precision == SKMMSE_MIXED_FP16)
+            return SKMMSE_ERR_UNSUPPORTED;
+        return SKMMSE_ERR_ARG;
+    }
+    if (p->flags & ~(SKMMSE_FLAG_TRACE | SKMMSE_FLAG_FORCE)) return SKMMSE_ERR_ARG;
+    if ((p->flags & SKMMSE_FLAG_FORCE) && !(p->flags & SKMMSE_FLAG_TRACE)) return SKMMSE_ERR_ARG;
+    return SKMMSE_OK;
+}
+
+skmmse_status validate_frame(const skmmse_frame& f) {
+    if (!f.frame || !f.mb_lost || !f.out) return SKMMSE_ERR_ARG;
+    if (f.width <= 0 || f.height <= 0 || (f.width & 1) || (f.height & 1)) return SKMMSE_ERR_SHAPE;
+    if (f.width > 65536 || f.height > 65536) return SKMMSE_ERR_SHAPE;
+    if (f.pitch < f.width || f.out_pitch < f.width) return SKMMSE_ERR_SHAPE;
+    if (f.out_f32 && f.out_f32_pitch < f.width) return SKMMSE_ERR_SHAPE;
+    if (f.out_f32 && (reinterpret_cast<uintptr_t>(f.out_f32) & 3)) return SKMMSE_ERR_ALIGN;
+    if (f.trace && (reinterpret_cast<uintptr_t>(f.trace) & 7)) return SKMMSE_ERR_ALIGN;
+    return SKMMSE_OK;
+}
+
+KParams make_kparams(const skmmse_params* p) {
+    KParams k;
+    std::memset(&k, 0, sizeof(k));
+    k.t_phi = p->t_phi;
+    k.log_t_nu = std::log(p->t_nu);
+    k.inv_2sig2 = (float)(1.0 / (2.0 * (double)p->sigma2));
+    k.ring_step = p->ring_step;
+    // the largest Chebyshev distance between a patch of the block and a candidate patch
+    // inside the 48x48 region is 28
+    k.nrings = (28 + p->ring_step - 1) / p->ring_step;
+    k.ridge_rel = p->ridge_rel;
+    k.beta_tie_rel = p->beta_tie_rel;
+    k.nbeta = p->beta_kmax - p->beta_kmin + 1;
+    for (int b = 0; b < k.nbeta; ++b) {
+        const double beta = std::pow(2.0, 0.5 * (p->beta_kmin + b));
+        k.inv2beta[b] = (float)(1.0 / (2.0 * beta));
+    }
+    k.concealed_is_support = p->concealed_is_support ? 1 : 0;
+    k.flags = p->flags;
+    return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+int skmmse_abi_version(void) { return SKMMSE_ABI_VERSION; }
+
+int skmmse_struct_size(int which) {
+    switch (which) {
+        case 0: return (int)sizeof(skmmse_trace_rec);
+        case 1: return (int)sizeof(skmmse_stats);
+        case 2: return (int)sizeof(skmmse_params);
+        case 3: return (int)sizeof(skmmse_frame);
+        default: return -1;
+    }
+}
+
+const char* skmmse_status_str(skmmse_status s) {
+    switch (s) {
+        case SKMMSE_OK: return "ok";
+        case SKMMSE_ERR_ARG: return "invalid argument";
+        case SKMMSE_ERR_SHAPE: return "unsupported frame shape";
+        case SKMMSE_ERR_ALIGN: return "unsupported alignment";
+        case SKMMSE_ERR_NOMEM: return "device memory allocation failed";
+        case SKMMSE_ERR_CUDA: return "CUDA runtime error";
+        case SKMMSE_ERR_TIMEOUT: return "dependency wait timed out on the device";
+        case SKMMSE_ERR_UNSUPPORTED: return "unsupported precision or flag";
+        default: return "unknown status";
+    }
+}
+
+void skmmse_params_preset(skmmse_params* p, int profile) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->t_phi = 20.0f;  // Table I: T_phi = 20 for all profiles
+    p->t_nu = profile == SKMMSE_EXPRESS ? 0.01f : profile == SKMMSE_EXCELLENT ? 100.0f : 0.1f;
+    p->sigma2 = 10.0f;  // Sec. IV-B
+    p->ring_step = 4;
+    p->ridge_rel = 1e-3f;
+    p->beta_kmin = -8;
+    p->beta_kmax = 16;
+    p->beta_tie_rel = 1e-3f;
+    p->concealed_is_support = 1;
+    p->precision = SKMMSE_FP32;
+    p->flags = 0;
+}
+
+skmmse_status skmmse_create(skmmse_context** out) {
+    if (!out) return SKMMSE_ERR_ARG;
+    *out = nullptr;
+    skmmse_context* c = new (std::nothrow) skmmse_context();
+    if (!c) return SKMMSE_ERR_NOMEM;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    c->smem_bytes = sizeof(sk::Smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sk::conceal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)c->smem_bytes);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm, sk::conceal_kernel,
+                                                          sk::kThreads, c->smem_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_stats, sk::kNStats * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e == cudaSuccess && q == cudaDriverEntryPointSuccess)
+            c->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        e = cudaSuccess;  // without the entry point every frame takes the plain-load path
+    }
+    if (e != cudaSuccess || c->blocks_per_sm < 1) {
+        skmmse_destroy(c);
+        (void)cudaGetLastError();
+        return SKMMSE_ERR_CUDA;
+    }
+    *out = c;
+    return SKMMSE_OK;
+}
+
+void skmmse_destroy(skmmse_context* c) {
+    if (!c) return;
+    if (c->stage_pending && c->stage_done) cudaEventSynchronize(c->stage_done);
+    if (c->d_arena) cudaFree(c->d_arena);
+    if (c->d_counters) cudaFree(c->d_counters);
+    if (c->d_stats) cudaFree(c->d_stats);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->stage_done) cudaEventDestroy(c->stage_done);
+    delete c;
+}
+
+skmmse_status skmmse_conceal_batch(skmmse_context* c, const skmmse_frame* frames, int n,
+                                   const skmmse_params* p, skmmse_stats* h_stats,
+                                   void* stream_v) {
+    if (!c || !frames || n < 1) return n < 1 && c && frames ? SKMMSE_ERR_SHAPE : SKMMSE_ERR_ARG;
+    if (n > 65536) return SKMMSE_ERR_SHAPE;
+    skmmse_status s = validate_params(p);
+    if (s != SKMMSE_OK) return s;
+    long long total_mbs = 0;
+    for (int i = 0; i < n; ++i) {
+        s = validate_frame(frames[i]);
+        if (s != SKMMSE_OK) return s;
+        const long long mbw = (frames[i].width + 15) / 16, mbh = (frames[i].height + 15) / 16;
+        total_mbs += mbw * mbh;
+    }
+    if (total_mbs > (1ll << 28)) return SKMMSE_ERR_SHAPE;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+
+    // arena layout
+    size_t off = 0;
+    const size_t o_frames = off; off = align_up(off + sizeof(FrameDev) * n, 128);
+    const size_t o_tmaps = off; off = align_up(off + sizeof(CUtensorMap) * n, 128);
+    const size_t o_eom = off; off = align_up(off + sizeof(int) * total_mbs, 128);
+    const size_t o_ent = off; off = align_up(off + sizeof(int4) * total_mbs, 128);
+    const size_t o_done = off; off = align_up(off + sizeof(unsigned) * total_mbs, 128);
+    const size_t o_vals = off; off = align_up(off + sizeof(float) * 256 * total_mbs, 128);
+    const size_t need = off;
+    if (need > c->arena_bytes) {
+        if (c->stage_pending) cudaEventSynchronize(c->stage_done);
+        SK_CHECK(cudaStreamSynchronize(stream));
+        if (c->d_arena) cudaFree(c->d_arena);
+        c->d_arena = nullptr;
+        c->arena_bytes = 0;
+        SK_CHECK(cudaMalloc(&c->d_arena, need));
+        c->arena_bytes = need;
+    }
+    const size_t stage_need = o_eom;  // frames + tmaps
+    if (stage_need > c->h_stage_bytes) {
+        if (c->stage_pending) cudaEventSynchronize(c->stage_done);
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        c->h_stage = nullptr;
+        c->h_stage_bytes = 0;
+        SK_CHECK(cudaMallocHost(&c->h_stage, stage_need));
+        c->h_stage_bytes = stage_need;
+    }
+    if (c->stage_pending) {  // the previous call's upload must have left the staging area
+        SK_CHECK(cudaEventSynchronize(c->stage_done));
+        c->stage_pending = false;
+    }
+    FrameDev* hf = reinterpret_cast<FrameDev*>(c->h_stage + o_frames);
+    CUtensorMap* ht = reinterpret_cast<CUtensorMap*>(c->h_stage + o_tmaps);
+    long long mb_base = 0;
+    for (int i = 0; i < n; ++i) {
+        const skmmse_frame& f = frames[i];
+        FrameDev& d = hf[i];
+        std::memset(&d, 0, sizeof(d));
+        d.in = f.frame;
+        d.out = f.out;
+        d.out_f32 = f.out_f32;
+        d.lost = f.mb_lost;
+        d.trace = (p->flags & SKMMSE_FLAG_TRACE) ? f.trace : nullptr;
+        d.w = f.width;
+        d.h = f.height;
+        d.pitch = f.pitch;
+        d.out_pitch = f.out_pitch;
+        d.out_f32_pitch = f.out_f32 ? f.out_f32_pitch : 0;
+        d.mbw = (f.width + 15) / 16;
+        d.mbh = (f.height + 15) / 16;
+        d.mb_base = (int)mb_base;
+        mb_base += (long long)d.mbw * d.mbh;
+        std::memset(&ht[i], 0, sizeof(CUtensorMap));
+        d.use_tma = 0;
+        const bool aligned = (reinterpret_cast<uintptr_t>(f.frame) % 16 == 0) && (f.pitch % 16 == 0);
+        if (c->encode && aligned) {
+            cuuint64_t gdim[2] = {(cuuint64_t)f.width, (cuuint64_t)f.height};
+            cuuint64_t gstride[1] = {(cuuint64_t)f.pitch};
+            cuuint32_t box[2] = {(cuuint32_t)sk::kReg, (cuuint32_t)sk::kReg};
+            cuuint32_t estr[2] = {1, 1};
+            CUresult r = c->encode(&ht[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                                   const_cast<uint8_t*>(f.frame), gdim, gstride, box, estr,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            d.use_tma = (r == CUDA_SUCCESS) ? 1 : 0;
+        }
+    }
+    // received pixels -> out
+    for (int i = 0; i < n; ++i) {
+        const skmmse_frame& f = frames[i];
+        if (f.out != f.frame)
+            SK_CHECK(cudaMemcpy2DAsync(f.out, f.out_pitch, f.frame, f.pitch, f.width, f.height,
+                                       cudaMemcpyDeviceToDevice, stream));
+    }
+    SK_CHECK(cudaMemcpyAsync(c->d_arena, c->h_stage, stage_need, cudaMemcpyHostToDevice, stream));
+    SK_CHECK(cudaEventRecord(c->stage_done, stream));
+    c->stage_pending = true;
+    SK_CHECK(cudaMemsetAsync(c->d_counters, 0, 4 * sizeof(int), stream));
+    SK_CHECK(cudaMemsetAsync(c->d_stats, 0, sk::kNStats * sizeof(unsigned long long), stream));
+
+    WorkDev w;
+    w.frames = reinterpret_cast<const FrameDev*>(c->d_arena + o_frames);
+    w.tmaps = reinterpret_cast<const CUtensorMap*>(c->d_arena + o_tmaps);
+    w.nframes = n;
+    w.entry_of_mb = reinterpret_cast<int*>(c->d_arena + o_eom);
+    w.entries = reinterpret_cast<int4*>(c->d_arena + o_ent);
+    w.counters = c->d_counters;
+    w.done = reinterpret_cast<unsigned*>(c->d_arena + o_done);
+    w.vals = reinterpret_cast<float*>(c->d_arena + o_vals);
+    w.stats = c->d_stats;
+    const KParams kp = make_kparams(p);
+    c->last_nbeta = kp.nbeta;
+
+    sk::build_queue_kernel<<<n, sk::kThreads, 0, stream>>>(w);
+    SK_CHECK(cudaGetLastError());
+    long long grid = (long long)c->sm_count * c->blocks_per_sm;
+    if (grid > total_mbs) grid = total_mbs;
+    if (grid < 1) grid = 1;
+    sk::conceal_kernel<<<(unsigned)grid, sk::kThreads, c->smem_bytes, stream>>>(w, kp);
+    SK_CHECK(cudaGetLastError());
+    if (h_stats) return skmmse_read_stats(c, h_stats, stream_v);
+    return SKMMSE_OK;
+}
+
+skmmse_status skmmse_conceal(skmmse_context* c, const uint8_t* d_frame, int width, int height,
+                             int pitch, const uint8_t* d_mb_lost, const skmmse_params* p,
+                             uint8_t* d_out, int out_pitch, float* d_out_f32,
+                             skmmse_stats* h_stats, void* stream) {
+    skmmse_frame f;
+    std::memset(&f, 0, sizeof(f));
+    f.frame = d_frame;
+    f.width = width;
+    f.height = height;
+    f.pitch = pitch;
+    f.mb_lost = d_mb_lost;
+    f.out = d_out;
+    f.out_pitch = out_pitch;
+    f.out_f32 = d_out_f32;
+    f.out_f32_pitch = width;
+    return skmmse_conceal_batch(c, &f, 1, p, h_stats, stream);
+}
+
+skmmse_status skmmse_read_stats(skmmse_context* c, skmmse_stats* h, void* stream_v) {
+    if (!c || !h) return SKMMSE_ERR_ARG;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    unsigned long long raw[sk::kNStats];
+    int counters[4];
+    SK_CHECK(cudaMemcpyAsync(raw, c->d_stats, sizeof(raw), cudaMemcpyDeviceToHost, stream));
+    SK_CHECK(cudaMemcpyAsync(counters, c->d_counters, sizeof(counters), cudaMemcpyDeviceToHost, stream));
+    SK_CHECK(cudaStreamSynchronize(stream));
+    std::memset(h, 0, sizeof(*h));
+    long long* dst = &h->n_lost_mbs;
+    for (int i = 0; i < sk::ST_COUNT; ++i) dst[i] = (long long)raw[i];
+    h->n_beta = c->last_nbeta;
+    h->error = counters[2];
+    return counters[2] ? SKMMSE_ERR_TIMEOUT : SKMMSE_OK;
+}
+
+}  // extern "C"

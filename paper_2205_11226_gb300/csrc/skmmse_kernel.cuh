@@ -1,0 +1,1459 @@
+// SK-MMSE concealment kernel for sm_103a (GB300).
+//
+// One persistent launch drains a work queue holding every lost 16x16 block of every
+// frame of a call.  A CTA of 256 threads owns one block at a time:
+//   1. stage the 48x48 support region (the block and its 8 neighbours, Sec. II) into
+//      shared memory: received pixels arrive by one TMA tile load of the 8-bit frame,
+//      pixels of blocks concealed earlier (when they are support) are read from the
+//      per-block FP32 results of the producing CTA after an acquire on its done flag;
+//   2. run the sequential fill of the block's 2x2 patches (Sec. II / end of Sec. III),
+//      one patch per step, every step parallel across candidates:
+//        - next patch: most available pixels in its 6x6 window (ties: lowest index);
+//        - context y0, flatness phi (Eq. (17)) and BRL (Eq. (16));
+//        - IDL (Eq. (15)) over rings of growing Chebyshev radius with a max-subtracted
+//          online softmax and the nu test of Eq. (18) after each ring;
+//        - HQL (Eq. (13)): exact covariance, double-float Cholesky and inverse factor,
+//          whitened distances, beta grid (Eqs. (9)-(10)), I0 by radix select and the
+//          closed-form alpha of Eq. (11);
+//        - clip, write back into the support;
+//   3. publish the block (release) and fetch the next queue entry.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "df.cuh"
+
+namespace sk {
+
+constexpr int kMB = 16;
+constexpr int kReg = 48;         // support region side
+constexpr int kWin = 6;          // context window side
+constexpr int kNpos = kReg - kWin + 1;  // 43 window positions per axis
+constexpr int kNcand = kNpos * kNpos;   // 1849
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxNy = 32;
+constexpr int kCh = 64;          // HQL candidate chunk
+constexpr int kZs = 40;          // staged row: x'(4) y'(32) one(1) pad(3)
+constexpr int kMaxBeta = 32;
+constexpr int kMaxI0 = 33;
+constexpr int kNStats = 32;
+
+// stats slots (match skmmse_stats field order)
+enum {
+    ST_LOST = 0, ST_PATCH, ST_EMPTY, ST_BRL, ST_IDL, ST_HQL, ST_NOCAND,
+    ST_RING0,  // 16 slots
+    ST_IDL_EVALS = ST_RING0 + 16, ST_IDL_NY, ST_HQL_M, ST_HQL_MNY, ST_HQL_I0M, ST_FLOPS,
+    ST_COUNT
+};
+static_assert(ST_COUNT <= kNStats, "stats slots");
+
+enum { L_EMPTY = 0, L_BRL = 1, L_IDL = 2, L_HQL = 3, L_NOCAND = 4 };
+
+struct KParams {
+    float t_phi;
+    float log_t_nu;
+    float inv_2sig2;      // 1 / (2 sigma^2)
+    int ring_step;
+    int nrings;
+    float ridge_rel;
+    float beta_tie_rel;
+    int nbeta;
+    float inv2beta[kMaxBeta];  // 1 / (2 beta_b), beta_b = 2^((kmin+b)/2)
+    int concealed_is_support;
+    unsigned flags;
+};
+
+struct FrameDev {
+    const uint8_t* in;
+    uint8_t* out;
+    float* out_f32;
+    const uint8_t* lost;
+    void* trace;
+    int w, h, pitch, out_pitch, out_f32_pitch;
+    int mbw, mbh;
+    int mb_base;  // offset of this frame's blocks in entry_of_mb
+    int use_tma;
+    int pad[3];
+};
+
+struct WorkDev {
+    const FrameDev* frames;
+    const CUtensorMap* tmaps;
+    int nframes;
+    int* entry_of_mb;         // per block of all frames: queue entry or -1
+    int4* entries;            // (frame, block index, rank among the frame's lost blocks, 0)
+    int* counters;            // [0] entries, [1] queue head, [2] error word
+    unsigned* done;           // per entry: 0 pending, 1 done, 2 done with error
+    float* vals;              // per entry: 256 unrounded values of the block
+    unsigned long long* stats;
+};
+
+struct TraceRec {             // layout of skmmse_trace_rec
+    int32_t mb;
+    int16_t step, patch;
+    int8_t layer, ring, beta_idx, n0;
+    int16_t ny, m;
+    float phi, log_nu, alpha, eps_best;
+    float x[4];
+    uint16_t i0[36];
+};
+
+// ------------------------------------------------------------------------------------
+// shared memory
+
+struct __align__(16) HqlP1 {                 // covariance / factorisation phase
+    int cint[36][36];
+    float cfrac[36][37];
+    df32 A[32][33];
+    df32 X[32][33];
+};
+struct __align__(16) HqlP2 {                 // distance / beta / alpha phase
+    __align__(16) float U[kCh][36];  // whitened chunk
+    float W[kMaxI0][kCh + 4];  // weights (beta pass: [beta][j]; alpha pass: [i][j])
+    float accB[kMaxBeta][kZs];
+    float accI[kMaxI0][kZs];
+    __align__(16) float UI[kMaxI0][36];
+    float XI[kMaxI0][4];
+    float mI[kMaxI0];
+    float scaleI[kMaxI0];
+};
+
+struct __align__(16) Hql {
+    uint16_t cand[kNcand + 7];  // window top-left as S offset u*48+v
+    float d[kNcand + 7];
+    __align__(16) float Z[2][kCh][kZs];  // staged candidates, centred by the integer shift
+    __align__(16) float Linv[32][36];
+    float G[4][32];
+    df32 cxy[4][32];            // C_XY (double-float)
+    df32 K[4][32];              // C_XY C_YY^-1 (double-float)
+    df32 accBd[kMaxBeta][kZs];  // beta-pass sums (double-float)
+    __align__(16) float ys[36];  // y0 - shift (compacted)
+    short off[36];              // compacted context offsets rel. window top-left
+    int i0[kMaxI0];             // I0 candidate indices, ascending
+    float dmin;
+    int M, n0, bstar;
+    float eps[kMaxBeta];
+    df32 ebard[32];
+    df32 xt0d[4];
+    df32 corr[4];
+    float red[kWarps][4];
+    int scan[kWarps + 1];
+    int hist[256];
+    int sel[4];
+    float colN[36], colF[36];
+    float lam;
+    float alpha;
+    union {
+        HqlP1 p1;
+        HqlP2 p2;
+    };
+};
+
+struct __align__(16) IdlSlot {
+    float m, s0, sx[4];
+    int cnt;
+    int pad;
+};
+
+struct __align__(128) Smem {
+    uint8_t raw[kReg * kReg];          // TMA destination (2304 B)
+    unsigned long long mbar;
+    unsigned long long av[kReg];       // availability bits per region row
+    unsigned long long unfilled;       // patches still to fill
+    float S[kReg * kReg];              // support values (0 where unavailable)
+    int nbst[9];                       // neighbour status: 0 received, 1 concealed, 2 n/a
+    int nbent[9];
+    int entry;
+    int pad0;
+    unsigned long long st[kNStats];    // per-CTA counters
+    TraceRec tr;                       // trace record of the current step
+    union {
+        IdlSlot idl[2][kWarps];
+        Hql hql;
+    };
+};
+
+// ------------------------------------------------------------------------------------
+// small helpers
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// bounded wait on an mbarrier phase; returns false if the bound was reached
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                          unsigned max_iter) {
+    const unsigned a = smem_u32(bar);
+    for (unsigned it = 0; it < max_iter; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (it > 64) __nanosleep(128);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map,
+                                            unsigned long long* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// block-wide exclusive scan of one int per thread; returns the prefix, *total = sum
+__device__ __forceinline__ int block_exscan(int v, int* scratch /*kWarps+1*/, int* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) scratch[wid] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            int t = scratch[w];
+            scratch[w] = run;
+            run += t;
+        }
+        scratch[kWarps] = run;
+    }
+    __syncthreads();
+    const int r = scratch[wid] + x - v;
+    *total = scratch[kWarps];
+    __syncthreads();
+    return r;
+}
+
+// context of the current step, held by every thread
+struct StepCtx {
+    int pa, pb;          // patch row/column inside the block
+    int wr, wc;          // window top-left in region coordinates
+    unsigned long long ymask;  // 36 bits, window raster order
+    unsigned rowcfg[6];  // per window row: context bits | x bits
+    int ny;
+    float phi, mean;
+    float y0w[36];       // window values (0 where unavailable)
+};
+
+// candidate window (u, v) valid: every configured position available
+__device__ __forceinline__ bool cand_valid(const Smem& sm, const StepCtx& c, int u, int v) {
+    bool ok = true;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        const unsigned bits = (unsigned)(sm.av[u + r] >> v) & 63u;
+        ok = ok && ((c.rowcfg[r] & ~bits) == 0u);
+    }
+    return ok;
+}
+
+// squared Euclidean context distance of window (base = u*48+v), Eq. (15)
+__device__ __forceinline__ float ctx_dist(const float* S, const StepCtx& c, int base) {
+    float d = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 36; ++k) {
+        if ((c.ymask >> k) & 1ull) {
+            const float t = c.y0w[k] - S[base + (k / 6) * kReg + (k % 6)];
+            d = __fmaf_rn(t, t, d);
+        }
+    }
+    return d;
+}
+
+// ring k (1-based) enumeration: i-th position of the square annulus with Chebyshev
+// radius in (rin, rout] around the origin
+__device__ __forceinline__ void annulus_pos(int i, int rin, int rout, int* dy, int* dx) {
+    const int side = 2 * rout + 1, t = rout - rin, top = t * side;
+    if (i < top) {
+        *dy = -rout + i / side;
+        *dx = -rout + i % side;
+    } else if (i < 2 * top) {
+        const int q = i - top;
+        *dy = rin + 1 + q / side;
+        *dx = -rout + q % side;
+    } else {
+        const int q = i - 2 * top;
+        const int row = q / (2 * t), cc = q % (2 * t);
+        *dy = -rin + row;
+        *dx = cc < t ? -rout + cc : rin + 1 + (cc - t);
+    }
+}
+
+__device__ __forceinline__ void online_add(float s, float x0, float x1, float x2, float x3,
+                                           float& m, float& s0, float sx[4]) {
+    if (s > m) {
+        const float sc = expf(m - s);
+        s0 *= sc;
+        sx[0] *= sc; sx[1] *= sc; sx[2] *= sc; sx[3] *= sc;
+        m = s;
+    }
+    const float w = expf(s - m);
+    s0 += w;
+    sx[0] = __fmaf_rn(w, x0, sx[0]);
+    sx[1] = __fmaf_rn(w, x1, sx[1]);
+    sx[2] = __fmaf_rn(w, x2, sx[2]);
+    sx[3] = __fmaf_rn(w, x3, sx[3]);
+}
+
+__device__ __forceinline__ void slot_merge(float& m, float& s0, float sx[4], float m2, float s02,
+                                           const float sx2[4]) {
+    const float M = fmaxf(m, m2);
+    const float a = expf(m - M), b = expf(m2 - M);
+    s0 = s0 * a + s02 * b;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sx[q] = sx[q] * a + sx2[q] * b;
+    m = M;
+}
+
+constexpr float kNegBig = -1.0e30f;
+
+// ------------------------------------------------------------------------------------
+// IDL: Eq. (15) over growing rings; returns 1 accepted, 0 not accepted, -1 no candidate
+
+__device__ __forceinline__ int idl_step(Smem& sm, const KParams& P, const StepCtx& c, float xhat[4],
+                        int* ring_out, float* lognu_out, long long* evals) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int pr = c.wr + 2, pc = c.wc + 2;  // patch top-left (region)
+    const float inv_h = P.inv_2sig2 / (float)c.ny;
+    const float cen = rintf(c.mean);
+    float m = kNegBig, s0 = 0.0f, sx[4] = {0.f, 0.f, 0.f, 0.f};
+    int cnt = 0;
+    int accepted = 0, k = 1;
+    float lognu = -INFINITY;
+    int total_cnt = 0;
+    for (k = 1; k <= P.nrings; ++k) {
+        const int rin = (k - 1) * P.ring_step, rout = k * P.ring_step;
+        const int side = 2 * rout + 1, inner = 2 * rin + 1;
+        const int npos = side * side - inner * inner;
+        for (int i = tid; i < npos; i += kThreads) {
+            int dy, dx;
+            annulus_pos(i, rin, rout, &dy, &dx);
+            const int u = pr + dy - 2, v = pc + dx - 2;
+            if (u < 0 || v < 0 || u >= kNpos || v >= kNpos) continue;
+            if (!cand_valid(sm, c, u, v)) continue;
+            const int base = u * kReg + v;
+            const float d = ctx_dist(sm.S, c, base);
+            const float* X = &sm.S[base + 2 * kReg + 2];
+            online_add(-d * inv_h, X[0] - cen, X[1] - cen, X[kReg] - cen, X[kReg + 1] - cen, m,
+                       s0, sx);
+            ++cnt;
+        }
+        // warp combine
+        float wm = m, ws = s0, wx[4] = {sx[0], sx[1], sx[2], sx[3]};
+        int wc = cnt;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float m2 = __shfl_xor_sync(0xffffffffu, wm, o);
+            const float s2 = __shfl_xor_sync(0xffffffffu, ws, o);
+            float x2[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x2[q] = __shfl_xor_sync(0xffffffffu, wx[q], o);
+            wc += __shfl_xor_sync(0xffffffffu, wc, o);
+            slot_merge(wm, ws, wx, m2, s2, x2);
+        }
+        IdlSlot* slot = &sm.idl[k & 1][0];
+        if (lane == 0) {
+            slot[wid].m = wm;
+            slot[wid].s0 = ws;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) slot[wid].sx[q] = wx[q];
+            slot[wid].cnt = wc;
+        }
+        __syncthreads();
+        float bm = slot[0].m, bs = slot[0].s0, bx[4] = {slot[0].sx[0], slot[0].sx[1],
+                                                        slot[0].sx[2], slot[0].sx[3]};
+        int bc = slot[0].cnt;
+        for (int w = 1; w < kWarps; ++w) {
+            const float x2[4] = {slot[w].sx[0], slot[w].sx[1], slot[w].sx[2], slot[w].sx[3]};
+            slot_merge(bm, bs, bx, slot[w].m, slot[w].s0, x2);
+            bc += slot[w].cnt;
+        }
+        total_cnt = bc;
+        if (bc > 0) {
+            lognu = bm + logf(bs);
+            if (lognu >= P.log_t_nu) {
+                accepted = 1;
+                const float inv = 1.0f / bs;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) xhat[q] = cen + bx[q] * inv;
+                break;
+            }
+        }
+    }
+    if (tid == 0) *evals = total_cnt;
+    *ring_out = accepted ? k : P.nrings;
+    *lognu_out = lognu;
+    if (total_cnt == 0) return -1;
+    return accepted;
+}
+
+// ------------------------------------------------------------------------------------
+// HQL
+
+// stage candidates [c0, c0+n) into Z[buf]: x' (4), y' (ny), 1, zero padding
+__device__ __forceinline__ bool hql_stage(Smem& sm, int buf, int c0, int n, int nz,
+                                          float shift) {
+    Hql& h = sm.hql;
+    bool frac = false;
+    for (int idx = threadIdx.x; idx < kCh * kZs; idx += kThreads) {
+        const int j = idx / kZs, k = idx - j * kZs;
+        float v = 0.0f;
+        if (j < n) {
+            const int base = h.cand[c0 + j];
+            if (k < nz) {
+                int o;
+                if (k < 4) o = (k >> 1) * kReg + (k & 1) + 2 * kReg + 2;
+                else o = h.off[k - 4];
+                v = sm.S[base + o] - shift;
+                frac = frac || (v != rintf(v));
+            } else if (k == 36) {
+                v = 1.0f;
+            }
+        }
+        h.Z[buf][j][k] = v;
+    }
+    return frac;
+}
+
+// enumerate the 44 covariance tiles (ta <= tb, not (0,0)) of the 9x9 grid of 4x4 tiles
+__device__ __forceinline__ void cov_tile(int t, int* ta, int* tb) {
+    int idx = t + 1;  // skip (0,0)
+    int a = 0;
+    while (idx >= 9 - a) {
+        idx -= 9 - a;
+        ++a;
+    }
+    *ta = a;
+    *tb = a + idx;
+}
+
+__device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepCtx& c, float xhat[4],
+                         TraceRec* tr, bool trace) {
+    Hql& h = sm.hql;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int ny = c.ny, nz = ny + 4;
+    const float shift = rintf(c.mean);
+
+    // context lists (compacted, window raster order)
+    if (tid < 36 && ((c.ymask >> tid) & 1ull)) {
+        const int idx = __popcll(c.ymask & ((1ull << tid) - 1ull));
+        h.off[idx] = (short)((tid / 6) * kReg + (tid % 6));
+        h.ys[idx] = c.y0w[tid] - shift;
+    }
+    if (tid >= 64 && tid < 100 && tid - 64 >= ny) {  // zero padding of the lists
+        h.off[tid - 64] = 0;
+        h.ys[tid - 64] = 0.0f;
+    }
+
+    // H0: valid candidates, ascending window index (R5)
+    {
+        int cnt = 0;
+        unsigned flags = 0;
+        for (int q = 0; q < 8; ++q) {
+            const int p = tid * 8 + q;
+            if (p < kNcand) {
+                const int u = p / kNpos, v = p - (p / kNpos) * kNpos;
+                if (cand_valid(sm, c, u, v)) {
+                    flags |= 1u << q;
+                    ++cnt;
+                }
+            }
+        }
+        int total;
+        int pos = block_exscan(cnt, h.scan, &total);
+        for (int q = 0; q < 8; ++q)
+            if ((flags >> q) & 1u) {
+                const int p = tid * 8 + q;
+                h.cand[pos++] = (uint16_t)((p / kNpos) * kReg + (p % kNpos));
+            }
+        if (tid == 0) h.M = total;
+    }
+    __syncthreads();
+    const int M = h.M;
+
+    // H1: mean and covariance of z' = z - shift, Eq. (8).  Integer parts accumulate
+    // exactly (|n'| <= 255, at most kCh products per thread per chunk < 2^24), the
+    // fractional cross terms separately; the chunk sums go to int32.
+    int ta = 0, tb = 0;
+    const bool tile_thread = tid < 220;
+    const int grp = tid / 44;
+    if (tile_thread) cov_tile(tid % 44, &ta, &tb);
+    const bool tile_active = tile_thread && (4 * tb < nz);
+    int ci[16];
+    float cf[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        ci[q] = 0;
+        cf[q] = 0.0f;
+    }
+    float colN = 0.0f, colF = 0.0f;
+    for (int idx = tid; idx < 36 * 36; idx += kThreads) {
+        h.p1.cint[idx / 36][idx % 36] = 0;
+    }
+    const int nchunks = (M + kCh - 1) / kCh;
+    {
+        bool frac = hql_stage(sm, 0, 0, min(kCh, M), nz, shift);
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const int buf = ch & 1, c0 = ch * kCh, n = min(kCh, M - c0);
+            const bool any_frac = __syncthreads_or(frac) != 0;
+            if (tile_active) {
+                float ai[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) ai[q] = 0.0f;
+                for (int j = grp; j < n; j += 5) {
+                    const float4 za = *reinterpret_cast<const float4*>(&h.Z[buf][j][4 * ta]);
+                    const float4 zb = *reinterpret_cast<const float4*>(&h.Z[buf][j][4 * tb]);
+                    const float a[4] = {za.x, za.y, za.z, za.w};
+                    const float b[4] = {zb.x, zb.y, zb.z, zb.w};
+                    float na[4], nb[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        na[q] = rintf(a[q]);
+                        nb[q] = rintf(b[q]);
+                    }
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) ai[p * 4 + q] = __fmaf_rn(na[p], nb[q], ai[p * 4 + q]);
+                    if (any_frac) {
+#pragma unroll
+                        for (int p = 0; p < 4; ++p)
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const float fb = b[q] - nb[q], fa = a[p] - na[p];
+                                cf[p * 4 + q] = __fmaf_rn(na[p], fb, cf[p * 4 + q]);
+                                cf[p * 4 + q] = __fmaf_rn(fa, b[q], cf[p * 4 + q]);
+                            }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) ci[q] += __float2int_rn(ai[q]);
+            } else if (tid >= 220) {
+                const int k = tid - 220;
+                if (k < nz) {
+                    for (int j = 0; j < n; ++j) {
+                        const float v = h.Z[buf][j][k];
+                        const float nv = rintf(v);
+                        colN += nv;
+                        colF += v - nv;
+                    }
+                }
+            }
+            if (ch + 1 < nchunks) frac = hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), nz, shift);
+        }
+    }
+    __syncthreads();
+    if (tile_active) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) atomicAdd(&h.p1.cint[4 * ta + p][4 * tb + q], ci[p * 4 + q]);
+    }
+    for (int g = 0; g < 5; ++g) {
+        if (tile_active && grp == g) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float& dst = h.p1.cfrac[4 * ta + p][4 * tb + q];
+                    dst = (g == 0) ? cf[p * 4 + q] : dst + cf[p * 4 + q];
+                }
+        }
+        __syncthreads();
+    }
+    if (tid >= 220 && tid - 220 < 36) {
+        h.colN[tid - 220] = colN;
+        h.colF[tid - 220] = colF;
+    }
+    __syncthreads();
+
+    // finalise C_ab = S_ab/M - T_a T_b / M^2 in double-float; YY (+ridge later), XY
+    {
+        const df32 invM = df_div(df_make(1.0f), df_make((float)M));
+        for (int idx = tid; idx < 36 * 36; idx += kThreads) {
+            const int a = idx / 36, b = idx % 36;
+            if (a > b || b < 4 || b >= nz) continue;
+            const df32 S = df_add(df_from_int(h.p1.cint[a][b]), df_make(h.p1.cfrac[a][b]));
+            const df32 Ta = df_two_sum(h.colN[a], h.colF[a]);
+            const df32 Tb = df_two_sum(h.colN[b], h.colF[b]);
+            const df32 Cab = df_sub(df_mul(S, invM), df_mul(df_mul(Ta, invM), df_mul(Tb, invM)));
+            if (a >= 4) {
+                h.p1.A[b - 4][a - 4] = Cab;  // lower triangle (row >= col)
+            } else {
+                h.cxy[a][b - 4] = Cab;
+            }
+        }
+    }
+    __syncthreads();
+    // ridge (R7): lambda = ridge_rel * tr(C_YY)/Ny + 1e-6
+    if (wid == 0) {
+        df32 t = lane < ny ? h.p1.A[lane][lane] : df_make(0.0f);
+        for (int o = 16; o > 0; o >>= 1) {
+            df32 u;
+            u.hi = __shfl_xor_sync(0xffffffffu, t.hi, o);
+            u.lo = __shfl_xor_sync(0xffffffffu, t.lo, o);
+            t = df_add(t, u);
+        }
+        const df32 lam = df_add(df_mul_f(df_div(t, df_make((float)ny)), P.ridge_rel), df_make(1e-6f));
+        __syncwarp();
+        if (lane < ny) h.p1.A[lane][lane] = df_add(h.p1.A[lane][lane], lam);
+        if (lane == 0) h.lam = df_to_f(lam);
+    }
+    for (int idx = tid; idx < 32 * 33; idx += kThreads) h.p1.X[idx / 33][idx % 33] = df_make(0.0f);
+    __syncthreads();
+
+    // Cholesky / inverse factor in double-float: Gaussian elimination A = Lu D Lu^T and
+    // the same row operations applied to I give X = Lu^-1; then L^-1 = D^-1/2 X.
+    {
+        int pi[3], pj[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int p = tid + q * kThreads;
+            int i = (int)((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);
+            while ((i + 1) * (i + 2) / 2 <= p) ++i;
+            while (i * (i + 1) / 2 > p) --i;
+            pi[q] = (p < 528) ? i : 99;
+            pj[q] = p - i * (i + 1) / 2;
+        }
+        for (int k = 0; k < ny; ++k) {
+            const df32 akk = h.p1.A[k][k];
+            const df32 rinv = df_div(df_make(1.0f), akk);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int i = pi[q], j = pj[q];
+                if (i >= ny || i <= k) continue;
+                const df32 mlt = df_mul(h.p1.A[i][k], rinv);
+                if (j > k) {
+                    h.p1.A[i][j] = df_sub(h.p1.A[i][j], df_mul(mlt, h.p1.A[j][k]));
+                } else if (j == k) {
+                    h.p1.X[i][k] = df_neg(mlt);
+                } else {
+                    h.p1.X[i][j] = df_sub(h.p1.X[i][j], df_mul(mlt, h.p1.X[k][j]));
+                }
+            }
+            __syncthreads();
+        }
+        // L^-1 = D^-1/2 X: kept in double-float in X, rounded to FP32 in Linv
+        for (int idx = tid; idx < 32 * 32; idx += kThreads) {
+            const int i = idx >> 5, j = idx & 31;
+            float v = 0.0f;
+            if (i < ny && j <= i) {
+                const df32 rs = df_div(df_make(1.0f), df_sqrt(h.p1.A[i][i]));
+                const df32 l = (j == i) ? rs : df_mul(h.p1.X[i][j], rs);
+                v = df_to_f(l);
+                h.p1.X[i][j] = l;
+            }
+            h.Linv[i][j] = v;
+        }
+    }
+    __syncthreads();
+    // G = C_XY L^-T (4 x ny): G[a][i] = sum_k C_XY[a][k] Linv[i][k], in double-float;
+    // kept in FP32 for the leave-one-out corrections and in double-float (in the first
+    // rows of A, no longer needed) for K
+    if (tid < 128) {
+        const int a = tid >> 5, i = tid & 31;
+        df32 g = df_make(0.0f);
+        if (i < ny)
+            for (int k = 0; k <= i; ++k) g = df_add(g, df_mul(h.cxy[a][k], h.p1.X[i][k]));
+        h.G[a][i] = df_to_f(g);
+        h.p1.A[a][i] = g;
+    }
+    __syncthreads();
+    // K = C_XY C_YY^-1 = G L^-1: K[a][j] = sum_{i >= j} G[a][i] Linv[i][j] (double-float)
+    if (tid < 128) {
+        const int a = tid >> 5, j = tid & 31;
+        df32 kk = df_make(0.0f);
+        if (j < ny)
+            for (int i = j; i < ny; ++i) kk = df_add(kk, df_mul(h.p1.A[a][i], h.p1.X[i][j]));
+        h.K[a][j] = kk;
+    }
+
+    // H2: whitened distances d_j = ||L^-1 (y_j - y0)||^2 (Mahalanobis, Eq. (6) with C_YY)
+    // thread tile: 2 candidates x 4 whitened coordinates
+    const int tj = (tid >> 3) * 2, tq = tid & 7;
+    auto whiten_tile = [&](int buf, float u0[4], float u1[4]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            u0[q] = 0.0f;
+            u1[q] = 0.0f;
+        }
+        for (int l4 = 0; l4 <= tq; ++l4) {
+            if (4 * l4 >= ny) break;
+            const float4 e0v = *reinterpret_cast<const float4*>(&h.Z[buf][tj][4 + 4 * l4]);
+            const float4 e1v = *reinterpret_cast<const float4*>(&h.Z[buf][tj + 1][4 + 4 * l4]);
+            const float4 ysv = *reinterpret_cast<const float4*>(&h.ys[4 * l4]);
+            const float e0[4] = {e0v.x - ysv.x, e0v.y - ysv.y, e0v.z - ysv.z, e0v.w - ysv.w};
+            const float e1[4] = {e1v.x - ysv.x, e1v.y - ysv.y, e1v.z - ysv.z, e1v.w - ysv.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 lv = *reinterpret_cast<const float4*>(&h.Linv[4 * tq + q][4 * l4]);
+                const float L4[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    u0[q] = __fmaf_rn(L4[r], e0[r], u0[q]);
+                    u1[q] = __fmaf_rn(L4[r], e1[r], u1[q]);
+                }
+            }
+        }
+    };
+    float lmin = INFINITY;
+    {
+        bool dummy = hql_stage(sm, 0, 0, min(kCh, M), nz, shift);
+        (void)dummy;
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const int buf = ch & 1, c0 = ch * kCh, n = min(kCh, M - c0);
+            __syncthreads();
+            float u0[4], u1[4];
+            whiten_tile(buf, u0, u1);
+            float p0 = 0.0f, p1 = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                p0 = __fmaf_rn(u0[q], u0[q], p0);
+                p1 = __fmaf_rn(u1[q], u1[q], p1);
+            }
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+                p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+            }
+            if (tq == 0) {
+                if (tj < n) {
+                    h.d[c0 + tj] = p0;
+                    lmin = fminf(lmin, p0);
+                }
+                if (tj + 1 < n) {
+                    h.d[c0 + tj + 1] = p1;
+                    lmin = fminf(lmin, p1);
+                }
+            }
+            if (ch + 1 < nchunks) {
+                bool d2 = hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), nz, shift);
+                (void)d2;
+            }
+        }
+    }
+    lmin = warp_max(-lmin);
+    if (lane == 0) h.red[wid][0] = -lmin;
+    __syncthreads();
+    if (tid == 0) {
+        float mn = h.red[0][0];
+        for (int w = 1; w < kWarps; ++w) mn = fminf(mn, h.red[w][0]);
+        h.dmin = mn;
+    }
+    __syncthreads();
+    const float dmin = h.dmin;
+
+    // H3: beta grid, Eqs. (9)-(10): accB[b][k] = sum_j w_j(b) z'_j[k], column 36 = sum w
+    const int nb = P.nbeta;
+    // tiles: one beta x 4 columns; thread owns tiles tid and tid + 256 (nb <= 32)
+    // per-chunk FP32 partial sums are added into double-float accumulators, so the
+    // rounding error does not grow with the number of candidates
+    const int bt0 = tid / 10, kq0 = tid % 10, bt1 = (tid + kThreads) / 10, kq1 = (tid + kThreads) % 10;
+    df32 ab0[4], ab1[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        ab0[q] = df_make(0.0f);
+        ab1[q] = df_make(0.0f);
+    }
+    auto beta_weights = [&](int buf, int c0, int n) {
+        for (int idx = tid; idx < kMaxBeta * kCh; idx += kThreads) {
+            const int b = idx / kCh, j = idx % kCh;
+            float w = 0.0f;
+            if (b < nb && j < n) w = expf(-(h.d[c0 + j] - dmin) * P.inv2beta[b]);
+            h.p2.W[b][j] = w;  // rows 0..31 of W (kMaxBeta <= kMaxI0)
+        }
+        (void)buf;
+    };
+    {
+        bool dd = hql_stage(sm, 0, 0, min(kCh, M), nz, shift);
+        (void)dd;
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const int buf = ch & 1, c0 = ch * kCh, n = min(kCh, M - c0);
+            __syncthreads();  // previous chunk's accumulation done, stage(buf) done
+            beta_weights(buf, c0, n);
+            __syncthreads();
+            auto beta_acc = [&](int bt, int kq, df32* abd) {
+                if (bt >= nb) return;
+                float ab[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int j = 0; j < n; ++j) {
+                    const float w = h.p2.W[bt][j];
+                    const float4 z = *reinterpret_cast<const float4*>(&h.Z[buf][j][4 * kq]);
+                    ab[0] = __fmaf_rn(w, z.x, ab[0]);
+                    ab[1] = __fmaf_rn(w, z.y, ab[1]);
+                    ab[2] = __fmaf_rn(w, z.z, ab[2]);
+                    ab[3] = __fmaf_rn(w, z.w, ab[3]);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) abd[q] = df_add(abd[q], df_make(ab[q]));
+            };
+            beta_acc(bt0, kq0, ab0);
+            beta_acc(bt1, kq1, ab1);
+            if (ch + 1 < nchunks) {
+                bool d2 = hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), nz, shift);
+                (void)d2;
+            }
+        }
+    }
+    if (bt0 < nb) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            h.p2.accB[bt0][4 * kq0 + q] = df_to_f(ab0[q]);
+            h.accBd[bt0][4 * kq0 + q] = ab0[q];
+        }
+    }
+    if (bt1 < nb) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            h.p2.accB[bt1][4 * kq1 + q] = df_to_f(ab1[q]);
+            h.accBd[bt1][4 * kq1 + q] = ab1[q];
+        }
+    }
+    __syncthreads();
+    // eps_y(b) = || y0 - y~0(b) ||^2 ; warp w handles b = w, w+8, ...
+    for (int b = wid; b < nb; b += kWarps) {
+        const float inv = 1.0f / h.p2.accB[b][36];
+        float e = 0.0f;
+        if (lane < ny) {
+            const float r = h.p2.accB[b][4 + lane] * inv - h.ys[lane];
+            e = r * r;
+        }
+        e = warp_sum(e);
+        if (lane == 0) h.eps[b] = e;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float emin = h.eps[0];
+        for (int b = 1; b < nb; ++b) emin = fminf(emin, h.eps[b]);
+        int bs = 0;
+        for (int b = 0; b < nb; ++b)
+            if (h.eps[b] <= emin * (1.0f + P.beta_tie_rel)) {
+                bs = b;
+                break;
+            }
+        h.bstar = bs;
+    }
+    __syncthreads();
+    const int bstar = h.bstar;
+    // x~0 and e-bar = y~0 - y0 (relative to the shift) at beta*, Eqs. (4)-(5)
+    if (tid < 36) {
+        const df32 sw = h.accBd[bstar][36];
+        if (tid < 4) h.xt0d[tid] = df_div(h.accBd[bstar][tid], sw);
+        else if (tid - 4 < ny) h.ebard[tid - 4] = df_sub(df_div(h.accBd[bstar][tid], sw), df_make(h.ys[tid - 4]));
+    }
+    __syncthreads();
+    // the correction of Eq. (13): K (y0 - y~0) = -K e-bar (double-float)
+    if (wid == 0) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            df32 t = (lane < ny) ? df_mul(h.K[a][lane], h.ebard[lane]) : df_make(0.0f);
+            for (int o = 16; o > 0; o >>= 1) {
+                df32 u;
+                u.hi = __shfl_xor_sync(0xffffffffu, t.hi, o);
+                u.lo = __shfl_xor_sync(0xffffffffu, t.lo, o);
+                t = df_add(t, u);
+            }
+            if (lane == 0) h.corr[a] = df_neg(t);
+        }
+    }
+
+    // H4: I0 = the n0 smallest d_j, ties to the lower index (radix select on the bits)
+    int n0 = min(ny + 1, M - 1);
+    if (n0 < 0) n0 = 0;
+    if (n0 > 0) {
+        unsigned prefix = 0, maskbits = 0;
+        int need = n0;
+        for (int shiftb = 24; shiftb >= 0; shiftb -= 8) {
+            for (int i = tid; i < 256; i += kThreads) h.hist[i] = 0;
+            __syncthreads();
+            for (int j = tid; j < M; j += kThreads) {
+                const unsigned key = __float_as_uint(h.d[j]);
+                if ((key & maskbits) == prefix) atomicAdd(&h.hist[(key >> shiftb) & 255u], 1);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int acc = 0, dg = 0;
+                for (dg = 0; dg < 256; ++dg) {
+                    if (acc + h.hist[dg] >= need) break;
+                    acc += h.hist[dg];
+                }
+                h.sel[0] = dg;
+                h.sel[1] = need - acc;
+            }
+            __syncthreads();
+            prefix |= (unsigned)h.sel[0] << shiftb;
+            maskbits |= 255u << shiftb;
+            need = h.sel[1];
+            __syncthreads();
+        }
+        // members: key < prefix, plus the first `need` with key == prefix (index order)
+        int cnt = 0;
+        unsigned f = 0, eqf = 0;
+        const int per = (M + kThreads - 1) / kThreads;  // <= 8
+        for (int q = 0; q < per; ++q) {
+            const int j = tid * per + q;
+            if (j < M) {
+                const unsigned key = __float_as_uint(h.d[j]);
+                if (key < prefix) f |= 1u << q;
+                if (key == prefix) eqf |= 1u << q;
+            }
+        }
+        int tot;
+        int eqpos = block_exscan(__popc(eqf), h.scan, &tot);
+        unsigned take = f;
+        for (int q = 0; q < per; ++q)
+            if ((eqf >> q) & 1u) {
+                if (eqpos < need) take |= 1u << q;
+                ++eqpos;
+            }
+        cnt = __popc(take);
+        int pos = block_exscan(cnt, h.scan, &tot);
+        for (int q = 0; q < per; ++q)
+            if ((take >> q) & 1u) h.i0[pos++] = tid * per + q;
+        __syncthreads();
+        // UI = L^-1 (y_i - y0), XI = x_i - shift
+        for (int idx = tid; idx < kMaxI0 * 36; idx += kThreads) {
+            const int i = idx / 36, k = idx % 36;
+            if (i >= n0) continue;
+            const int base = h.cand[h.i0[i]];
+            if (k < 32) {
+                float u = 0.0f;
+                if (k < ny)
+                    for (int l = 0; l <= k; ++l)
+                        u = __fmaf_rn(h.Linv[k][l], (sm.S[base + h.off[l]] - shift) - h.ys[l], u);
+                h.p2.UI[i][k] = u;
+            } else {
+                const int a = k - 32;
+                h.p2.XI[i][a] = sm.S[base + (a >> 1) * kReg + (a & 1) + 2 * kReg + 2] - shift;
+            }
+        }
+        if (tid < kMaxI0) {
+            h.p2.mI[tid] = kNegBig;
+        }
+    }
+    __syncthreads();
+
+    // H5: leave-one-out predictions for i in I0 at beta* (Eqs. (11)-(12))
+    float num = 0.0f, den = 0.0f;
+    if (n0 > 0) {
+        const float ib = P.inv2beta[bstar];
+        // accumulators: thread owns tiles (i, column quad) over accI[n0][40]
+        // tiles: one I0 member x 4 columns of [1 | x' | u]; thread owns tiles tid, tid+256
+        float acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
+        const int ti0 = tid / 10, tk0 = tid % 10;
+        const int ti1 = (tid + kThreads) / 10, tk1 = (tid + kThreads) % 10;
+        bool dd = hql_stage(sm, 0, 0, min(kCh, M), nz, shift);
+        (void)dd;
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const int buf = ch & 1, c0 = ch * kCh, n = min(kCh, M - c0);
+            __syncthreads();
+            // whitened chunk into U
+            {
+                float u0[4], u1[4];
+                whiten_tile(buf, u0, u1);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    h.p2.U[tj][4 * tq + q] = u0[q];
+                    h.p2.U[tj + 1][4 * tq + q] = u1[q];
+                }
+            }
+            __syncthreads();
+            // distances to the I0 members -> exponents in W
+            for (int idx = tid; idx < kMaxI0 * kCh; idx += kThreads) {
+                const int i = idx / kCh, j = idx % kCh;
+                float s = kNegBig;
+                if (i < n0 && j < n && (c0 + j) != h.i0[i]) {
+                    float dd2 = 0.0f;
+                    for (int k4 = 0; k4 < 8; ++k4) {
+                        if (4 * k4 >= ny) break;
+                        const float4 a = *reinterpret_cast<const float4*>(&h.p2.UI[i][4 * k4]);
+                        const float4 b = *reinterpret_cast<const float4*>(&h.p2.U[j][4 * k4]);
+                        float t;
+                        t = a.x - b.x; dd2 = __fmaf_rn(t, t, dd2);
+                        t = a.y - b.y; dd2 = __fmaf_rn(t, t, dd2);
+                        t = a.z - b.z; dd2 = __fmaf_rn(t, t, dd2);
+                        t = a.w - b.w; dd2 = __fmaf_rn(t, t, dd2);
+                    }
+                    s = -dd2 * ib;
+                }
+                h.p2.W[i][j] = s;
+            }
+            __syncthreads();
+            // online max per row, rescale factor, weights
+            for (int i = wid; i < n0; i += kWarps) {
+                const float s0v = h.p2.W[i][lane], s1v = h.p2.W[i][lane + 32];
+                const float cm = warp_max(fmaxf(s0v, s1v));
+                const float old = h.p2.mI[i];
+                const float nm = fmaxf(old, cm);
+                __syncwarp();
+                h.p2.W[i][lane] = (s0v <= kNegBig) ? 0.0f : expf(s0v - nm);
+                h.p2.W[i][lane + 32] = (s1v <= kNegBig) ? 0.0f : expf(s1v - nm);
+                if (lane == 0) {
+                    h.p2.scaleI[i] = expf(old - nm);
+                    h.p2.mI[i] = nm;
+                }
+            }
+            __syncthreads();
+            // acc[i][col] += sum_j W[i][j] * V[j][col], V = [1 | x' | u]
+            auto accum = [&](int ti, int tk, float* acc) {
+                if (ti >= n0) return;
+                const float sc = h.p2.scaleI[ti];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] *= sc;
+                for (int j = 0; j < n; ++j) {
+                    const float w = h.p2.W[ti][j];
+                    float v[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int col = 4 * tk + q;
+                        float x;
+                        if (col == 0) x = 1.0f;
+                        else if (col < 5) x = h.Z[buf][j][col - 1];
+                        else if (col < 37) x = h.p2.U[j][col - 5];
+                        else x = 0.0f;
+                        v[q] = x;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] = __fmaf_rn(w, v[q], acc[q]);
+                }
+            };
+            accum(ti0, tk0, acc0);
+            accum(ti1, tk1, acc1);
+            if (ch + 1 < nchunks) {
+                bool d2 = hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), nz, shift);
+                (void)d2;
+            }
+        }
+        if (ti0 < n0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) h.p2.accI[ti0][4 * tk0 + q] = acc0[q];
+        }
+        if (ti1 < n0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) h.p2.accI[ti1][4 * tk1 + q] = acc1[q];
+        }
+        __syncthreads();
+        // r_i = x_i - x~_i ; g_i = G (u_i - u~_i) ; alpha = sum r.g / sum g.g
+        if (tid < 4 * kMaxI0) {
+            const int i = tid >> 2, a = tid & 3;
+            if (i < n0) {
+                const float inv = 1.0f / h.p2.accI[i][0];
+                const float r = h.p2.XI[i][a] - h.p2.accI[i][1 + a] * inv;
+                float g = 0.0f;
+                for (int k = 0; k < ny; ++k)
+                    g = __fmaf_rn(h.G[a][k], h.p2.UI[i][k] - h.p2.accI[i][5 + k] * inv, g);
+                num = r * g;
+                den = g * g;
+            }
+        }
+    }
+    num = warp_sum(num);
+    den = warp_sum(den);
+    __syncthreads();
+    if (lane == 0) {
+        h.red[wid][0] = num;
+        h.red[wid][1] = den;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float nn = 0.0f, dd = 0.0f;
+        for (int w = 0; w < kWarps; ++w) {
+            nn += h.red[w][0];
+            dd += h.red[w][1];
+        }
+        float al = dd > 0.0f ? nn / dd : 0.0f;
+        al = fminf(fmaxf(al, 0.0f), 1.0f);
+        h.alpha = al;
+        h.n0 = n0;
+    }
+    __syncthreads();
+    const float alpha = h.alpha;
+    // x0_hat = x~0 + alpha C_XY C_YY^-1 (y0 - y~0), Eq. (13)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const df32 v = df_add(df_add(df_make(shift), h.xt0d[a]), df_mul_f(h.corr[a], alpha));
+        xhat[a] = df_to_f(v);
+    }
+    if (trace && tid == 0) {
+        tr->beta_idx = (int8_t)bstar;
+        tr->n0 = (int8_t)n0;
+        tr->alpha = alpha;
+        tr->eps_best = h.eps[bstar];
+        tr->m = (int16_t)M;
+        for (int t = 0; t < 36; ++t) {
+            if (t < n0) {
+                const int base = h.cand[h.i0[t]];
+                tr->i0[t] = (uint16_t)((base / kReg) * kNpos + base % kReg);
+            } else {
+                tr->i0[t] = 0xffff;
+            }
+        }
+    }
+    if (tid == 0) {
+        sm.st[ST_HQL_M] += M;
+        sm.st[ST_HQL_MNY] += (unsigned long long)M * ny;
+        sm.st[ST_HQL_I0M] += (unsigned long long)n0 * M;
+        // algorithmic FP32 operations of this HQL estimate (one exp counts as one):
+        // covariance (upper C_YY and C_XY), two whitening passes with the distance,
+        // beta grid (exp + weighted sums of 4+Ny+1 columns), leave-one-out pass
+        const unsigned long long Mu = M, nyu = ny, n0u = n0, nbu = P.nbeta;
+        sm.st[ST_FLOPS] += Mu * (nyu * (nyu + 1) + 8 * nyu + 2 * (nyu + 4)) +
+                           2 * Mu * (nyu * (nyu + 1) + 2 * nyu) +
+                           nbu * Mu * (2 * (nyu + 5) + 3) +
+                           n0u * Mu * (3 * nyu + 2 * (nyu + 5) + 3);
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------
+// the persistent kernel
+
+__global__ void __launch_bounds__(kThreads, 2) conceal_kernel(WorkDev W, KParams P) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const bool trace_on = (P.flags & 1u) != 0u;
+    const bool force_on = (P.flags & 2u) != 0u;
+
+    if (tid == 0) {
+        mbar_init(&sm.mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = tid; i < kNStats; i += kThreads) sm.st[i] = 0;
+    __syncthreads();
+    unsigned phase = 0;
+    const int n_entries = W.counters[0];
+
+    for (;;) {
+        if (tid == 0) sm.entry = atomicAdd(&W.counters[1], 1);
+        __syncthreads();
+        const int e = sm.entry;
+        if (e >= n_entries) break;
+        const int4 ent = W.entries[e];
+        const FrameDev& F = W.frames[ent.x];
+        const int mb = ent.y, mby = mb / F.mbw, mbx = mb - (mb / F.mbw) * F.mbw;
+        const int oy = mby * kMB - kMB, ox = mbx * kMB - kMB;
+
+        // neighbour status (R1)
+        if (tid < 9) {
+            const int ny_ = mby + tid / 3 - 1, nx_ = mbx + tid % 3 - 1;
+            int st = 2, en = -1;
+            if (ny_ >= 0 && nx_ >= 0 && ny_ < F.mbh && nx_ < F.mbw) {
+                const int q = F.mb_base + ny_ * F.mbw + nx_;
+                const int qe = W.entry_of_mb[q];
+                if (qe < 0) st = 0;
+                else if (P.concealed_is_support && (ny_ * F.mbw + nx_) < mb) {
+                    st = 1;
+                    en = qe;
+                }
+            }
+            sm.nbst[tid] = st;
+            sm.nbent[tid] = en;
+        }
+        // TMA: the 48x48 region of the 8-bit frame (out-of-frame reads fill zeros)
+        if (tid == 0 && F.use_tma) {
+            tmap_acquire(&W.tmaps[ent.x]);
+            mbar_expect_tx(&sm.mbar, kReg * kReg);
+            tma_load_2d(sm.raw, &W.tmaps[ent.x], &sm.mbar, ox, oy);
+        }
+        __syncthreads();
+        // dependency waits (bounded)
+        if (tid < 9 && sm.nbst[tid] == 1) {
+            const unsigned* flag = &W.done[sm.nbent[tid]];
+            unsigned it = 0;
+            while (ld_acquire(flag) == 0u) {
+                __nanosleep(200);
+                if (++it > (1u << 25)) {
+                    atomicExch(&W.counters[2], 6);
+                    sm.nbst[tid] = 2;
+                    break;
+                }
+            }
+        }
+        if (tid == 0 && F.use_tma) {
+            if (!mbar_wait(&sm.mbar, phase, 1u << 26)) {
+                atomicExch(&W.counters[2], 6);
+                mbar_wait(&sm.mbar, phase, 1u << 26);
+            }
+        }
+        phase ^= (F.use_tma ? 1u : 0u);
+        __syncthreads();
+        // convert to values + availability (ballot per row half)
+        for (int r = wid; r < kReg; r += kWarps) {
+            unsigned long long bits = 0;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int cc = half * 32 + lane;
+                bool av = false;
+                float v = 0.0f;
+                if (cc < kReg) {
+                    const int fy = oy + r, fx = ox + cc;
+                    if (fy >= 0 && fx >= 0 && fy < F.h && fx < F.w) {
+                        const int nb = (r / kMB) * 3 + cc / kMB;
+                        const int st = sm.nbst[nb];
+                        if (st == 0) {
+                            v = F.use_tma ? (float)sm.raw[r * kReg + cc]
+                                          : (float)F.in[(size_t)fy * F.pitch + fx];
+                            av = true;
+                        } else if (st == 1) {
+                            v = __ldcg(&W.vals[(size_t)sm.nbent[nb] * 256 + (r % kMB) * kMB + cc % kMB]);
+                            av = true;
+                        }
+                    }
+                    sm.S[r * kReg + cc] = v;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, av);
+                bits |= (unsigned long long)bal << (32 * half);
+            }
+            if (lane == 0) sm.av[r] = bits;
+        }
+        if (tid == 0) {
+            unsigned long long uf = 0;
+            for (int a = 0; a < 8; ++a)
+                for (int b = 0; b < 8; ++b)
+                    if (mby * kMB + 2 * a < F.h && mbx * kMB + 2 * b < F.w) uf |= 1ull << (a * 8 + b);
+            sm.unfilled = uf;
+            sm.st[ST_LOST] += 1;
+        }
+        __syncthreads();
+
+        TraceRec* trace_base =
+            (trace_on && F.trace) ? reinterpret_cast<TraceRec*>(F.trace) + (size_t)ent.z * 64 : nullptr;
+        const int npatch = __popcll(sm.unfilled);
+        for (int step = 0; step < npatch; ++step) {
+            StepCtx c;
+            // next patch (R2): most available pixels in the 6x6 window, lowest index
+            {
+                const unsigned long long uf = sm.unfilled;
+                int best = -1;
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int p = lane + 32 * h2;
+                    if ((uf >> p) & 1ull) {
+                        const int a = p >> 3, b = p & 7;
+                        const int wr = kMB + 2 * a - 2, wc = kMB + 2 * b - 2;
+                        int cnt = 0;
+#pragma unroll
+                        for (int r = 0; r < 6; ++r) cnt += __popc((unsigned)(sm.av[wr + r] >> wc) & 63u);
+                        const int key = cnt * 64 + (63 - p);
+                        best = max(best, key);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+                const int p = 63 - (best & 63);
+                c.pa = p >> 3;
+                c.pb = p & 7;
+            }
+            c.wr = kMB + 2 * c.pa - 2;
+            c.wc = kMB + 2 * c.pb - 2;
+            c.ymask = 0;
+#pragma unroll
+            for (int r = 0; r < 6; ++r) {
+                const unsigned bits = (unsigned)(sm.av[c.wr + r] >> c.wc) & 63u;
+                c.ymask |= (unsigned long long)bits << (6 * r);
+                c.rowcfg[r] = bits | ((r == 2 || r == 3) ? 12u : 0u);
+            }
+            c.ny = __popcll(c.ymask);
+            float mx = -INFINITY, mn = INFINITY, sum = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 36; ++k) {
+                const float v = sm.S[(c.wr + k / 6) * kReg + c.wc + k % 6];
+                c.y0w[k] = v;
+                if ((c.ymask >> k) & 1ull) {
+                    mx = fmaxf(mx, v);
+                    mn = fminf(mn, v);
+                    sum += v;
+                }
+            }
+            c.phi = mx - mn;
+            c.mean = c.ny > 0 ? sum / (float)c.ny : 0.0f;
+
+            float xhat[4];
+            int layer;
+            int ring = 0;
+            float lognu = -INFINITY;
+            long long evals = 0;
+            if (trace_base && tid == 0) {
+                sm.tr.beta_idx = -1;
+                sm.tr.n0 = 0;
+                sm.tr.alpha = 0.0f;
+                sm.tr.eps_best = 0.0f;
+                sm.tr.m = 0;
+                for (int t = 0; t < 36; ++t) sm.tr.i0[t] = 0xffff;
+            }
+            if (c.ny == 0) {
+                layer = L_EMPTY;  // R3
+                xhat[0] = xhat[1] = xhat[2] = xhat[3] = 128.0f;
+            } else if (c.phi <= P.t_phi) {
+                layer = L_BRL;    // Eq. (16)
+                xhat[0] = xhat[1] = xhat[2] = xhat[3] = c.mean;
+            } else {
+                const int r = idl_step(sm, P, c, xhat, &ring, &lognu, &evals);
+                if (tid == 0) {
+                    sm.st[ST_IDL_EVALS] += evals;
+                    sm.st[ST_IDL_NY] += evals * c.ny;
+                    // per candidate: 3 Ny (difference, square, sum), exp, 5 weighted sums
+                    sm.st[ST_FLOPS] += evals * (3ull * c.ny + 11ull);
+                }
+                if (r == 1) {
+                    layer = L_IDL;
+                } else if (r < 0) {
+                    layer = L_NOCAND;
+                    xhat[0] = xhat[1] = xhat[2] = xhat[3] = c.mean;
+                } else {
+                    layer = L_HQL;
+                    __syncthreads();  // IDL slots -> HQL scratch
+                    hql_step(sm, P, c, xhat, &sm.tr, trace_base != nullptr);
+                }
+            }
+            // R8: clip and write back
+            if (tid == 0) {
+                const int pr = c.wr + 2, pc = c.wc + 2;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) xhat[a] = fminf(fmaxf(xhat[a], 0.0f), 255.0f);
+                float xw[4] = {xhat[0], xhat[1], xhat[2], xhat[3]};
+                if (force_on && trace_base) {  // verification hook: reference write-back
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) xw[a] = trace_base[step].x[a];
+                }
+                sm.S[pr * kReg + pc] = xw[0];
+                sm.S[pr * kReg + pc + 1] = xw[1];
+                sm.S[(pr + 1) * kReg + pc] = xw[2];
+                sm.S[(pr + 1) * kReg + pc + 1] = xw[3];
+                sm.av[pr] |= 3ull << pc;
+                sm.av[pr + 1] |= 3ull << pc;
+                sm.unfilled &= ~(1ull << (c.pa * 8 + c.pb));
+                sm.st[ST_PATCH] += 1;
+                sm.st[ST_FLOPS] += 3ull * c.ny;  // context gather, flatness, mean
+                sm.st[layer == L_EMPTY ? ST_EMPTY : layer == L_BRL ? ST_BRL : layer == L_IDL ? ST_IDL
+                      : layer == L_HQL ? ST_HQL : ST_NOCAND] += 1;
+                if (layer == L_IDL) sm.st[ST_RING0 + min(ring, 15)] += 1;
+                if (trace_base) {
+                    TraceRec& t = sm.tr;
+                    t.mb = mb;
+                    t.step = (int16_t)step;
+                    t.patch = (int16_t)(c.pa * 8 + c.pb);
+                    t.layer = (int8_t)layer;
+                    t.ring = (int8_t)ring;
+                    t.ny = (int16_t)c.ny;
+                    t.phi = c.phi;
+                    t.log_nu = lognu;
+                    for (int a = 0; a < 4; ++a) t.x[a] = xhat[a];
+                    trace_base[step] = t;
+                }
+            }
+            __syncthreads();
+        }
+
+        // publish: unrounded values for dependants, rounded / FP32 outputs
+        for (int i = tid; i < 256; i += kThreads) {
+            const int r = i >> 4, cc = i & 15;
+            const float v = sm.S[(kMB + r) * kReg + kMB + cc];
+            W.vals[(size_t)e * 256 + i] = v;
+            const int fy = mby * kMB + r, fx = mbx * kMB + cc;
+            if (fy < F.h && fx < F.w) {
+                F.out[(size_t)fy * F.out_pitch + fx] = (uint8_t)__float2int_rn(v);
+                if (F.out_f32) F.out_f32[(size_t)fy * F.out_f32_pitch + fx] = v;
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) st_release(&W.done[e], 1u);
+    }
+    __syncthreads();
+    for (int i = tid; i < ST_COUNT; i += kThreads)
+        if (sm.st[i]) atomicAdd(&W.stats[i], sm.st[i]);
+}
+
+// ------------------------------------------------------------------------------------
+// queue construction: one CTA per frame; entries of a frame in raster order
+
+__global__ void __launch_bounds__(kThreads) build_queue_kernel(WorkDev W) {
+    __shared__ int scan[kWarps + 1];
+    __shared__ int base_s;
+    const int f = blockIdx.x;
+    const FrameDev& F = W.frames[f];
+    const int nmb = F.mbw * F.mbh;
+    // count
+    int cnt = 0;
+    for (int i = threadIdx.x; i < nmb; i += kThreads) cnt += F.lost[i] != 0;
+    int total;
+    (void)block_exscan(cnt, scan, &total);
+    if (threadIdx.x == 0) base_s = atomicAdd(&W.counters[0], total);
+    __syncthreads();
+    const int base = base_s;
+    // ranks in raster order: process in tiles of kThreads
+    int run = 0;
+    for (int t0 = 0; t0 < nmb; t0 += kThreads) {
+        const int i = t0 + threadIdx.x;
+        const int lost = (i < nmb) ? (F.lost[i] != 0) : 0;
+        int tot;
+        const int r = block_exscan(lost, scan, &tot) + run;
+        if (i < nmb) {
+            if (lost) {
+                W.entry_of_mb[F.mb_base + i] = base + r;
+                W.entries[base + r] = make_int4(f, i, r, 0);
+                W.done[base + r] = 0u;
+            } else {
+                W.entry_of_mb[F.mb_base + i] = -1;
+            }
+        }
+        run += tot;
+    }
+}
+
+}  // namespace sk
+
+namespace sk {
+static_assert(sizeof(Smem) <= 113 * 1024, "two CTAs per SM");
+static_assert(offsetof(Hql, Z) % 16 == 0 && offsetof(Hql, Linv) % 16 == 0 &&
+                  offsetof(Hql, ys) % 16 == 0 && offsetof(Smem, hql) % 16 == 0,
+              "float4 operands");
+}  // namespace sk

@@ -1,0 +1,257 @@
+"""Python binding of the C-ABI library ``libskmmse.so`` (include/skmmse.h).
+
+Argument marshalling only: every step of the concealment runs in the CUDA kernels of
+the library.  PyTorch provides device memory and streams.  There is no fallback: if the
+library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libskmmse.so")
+
+EXPRESS, EFFICIENT, EXCELLENT = 0, 1, 2
+PROFILES = {"express": EXPRESS, "efficient": EFFICIENT, "excellent": EXCELLENT}
+FP32, MIXED_BF16, MIXED_FP16 = 0, 1, 2
+FLAG_TRACE = 1
+FLAG_FORCE = 2
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported frame shape", 3: "unsupported alignment",
+          4: "device memory allocation failed", 5: "CUDA runtime error",
+          6: "dependency wait timed out on the device", 7: "unsupported precision or flag"}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("t_phi", ctypes.c_float), ("t_nu", ctypes.c_float), ("sigma2", ctypes.c_float),
+        ("ring_step", ctypes.c_int), ("ridge_rel", ctypes.c_float), ("beta_kmin", ctypes.c_int),
+        ("beta_kmax", ctypes.c_int), ("beta_tie_rel", ctypes.c_float),
+        ("concealed_is_support", ctypes.c_int), ("precision", ctypes.c_int), ("flags", ctypes.c_uint),
+    ]
+
+
+class Frame(ctypes.Structure):
+    _fields_ = [
+        ("frame", ctypes.c_void_p), ("width", ctypes.c_int), ("height", ctypes.c_int),
+        ("pitch", ctypes.c_int), ("mb_lost", ctypes.c_void_p), ("out", ctypes.c_void_p),
+        ("out_pitch", ctypes.c_int), ("out_f32", ctypes.c_void_p), ("out_f32_pitch", ctypes.c_int),
+        ("trace", ctypes.c_void_p),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("n_lost_mbs", ctypes.c_longlong), ("n_patches", ctypes.c_longlong),
+        ("n_empty", ctypes.c_longlong), ("n_brl", ctypes.c_longlong), ("n_idl", ctypes.c_longlong),
+        ("n_hql", ctypes.c_longlong), ("n_brl_nocand", ctypes.c_longlong),
+        ("idl_ring_hist", ctypes.c_longlong * 16), ("idl_cand_evals", ctypes.c_longlong),
+        ("idl_ny_evals", ctypes.c_longlong), ("hql_cands", ctypes.c_longlong),
+        ("hql_ny_cands", ctypes.c_longlong), ("hql_i0_cands", ctypes.c_longlong),
+        ("alg_flops", ctypes.c_longlong), ("n_beta", ctypes.c_longlong), ("error", ctypes.c_int), ("pad", ctypes.c_int),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: (list(getattr(self, k)) if k == "idl_ring_hist" else int(getattr(self, k)))
+                for k, _ in self._fields_ if k != "pad"}
+
+
+TRACE_DTYPE = np.dtype([
+    ("mb", "<i4"), ("step", "<i2"), ("patch", "<i2"), ("layer", "i1"), ("ring", "i1"),
+    ("beta_idx", "i1"), ("n0", "i1"), ("ny", "<i2"), ("m", "<i2"), ("phi", "<f4"),
+    ("log_nu", "<f4"), ("alpha", "<f4"), ("eps_best", "<f4"), ("x", "<f4", (4,)),
+    ("i0", "<u2", (36,))])
+
+# every symbol include/skmmse.h declares
+EXPORTS = ["skmmse_abi_version", "skmmse_struct_size", "skmmse_status_str", "skmmse_params_preset",
+           "skmmse_create", "skmmse_destroy", "skmmse_conceal", "skmmse_conceal_batch",
+           "skmmse_read_stats"]
+
+_lib = None
+
+
+class SkmmseError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)} (status {status})")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load libskmmse.so (built by ``paper_2205_11226_gb300.build``).  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is missing: run paper_2205_11226_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    vp, ci = ctypes.c_void_p, ctypes.c_int
+    lib.skmmse_abi_version.restype = ci
+    lib.skmmse_struct_size.restype = ci
+    lib.skmmse_struct_size.argtypes = [ci]
+    lib.skmmse_status_str.restype = ctypes.c_char_p
+    lib.skmmse_status_str.argtypes = [ci]
+    lib.skmmse_params_preset.restype = None
+    lib.skmmse_params_preset.argtypes = [ctypes.POINTER(Params), ci]
+    lib.skmmse_create.restype = ci
+    lib.skmmse_create.argtypes = [ctypes.POINTER(vp)]
+    lib.skmmse_destroy.restype = None
+    lib.skmmse_destroy.argtypes = [vp]
+    lib.skmmse_conceal.restype = ci
+    lib.skmmse_conceal.argtypes = [vp, vp, ci, ci, ci, vp, ctypes.POINTER(Params), vp, ci, vp,
+                                   ctypes.POINTER(Stats), vp]
+    lib.skmmse_conceal_batch.restype = ci
+    lib.skmmse_conceal_batch.argtypes = [vp, ctypes.POINTER(Frame), ci, ctypes.POINTER(Params),
+                                         ctypes.POINTER(Stats), vp]
+    lib.skmmse_read_stats.restype = ci
+    lib.skmmse_read_stats.argtypes = [vp, ctypes.POINTER(Stats), vp]
+    assert lib.skmmse_struct_size(0) == TRACE_DTYPE.itemsize, "trace record layout"
+    assert lib.skmmse_struct_size(1) == ctypes.sizeof(Stats), "stats layout"
+    assert lib.skmmse_struct_size(2) == ctypes.sizeof(Params), "params layout"
+    assert lib.skmmse_struct_size(3) == ctypes.sizeof(Frame), "frame layout"
+    _lib = lib
+    return lib
+
+
+def params(profile: str | int = "efficient", **kw) -> Params:
+    lib = load()
+    p = Params()
+    lib.skmmse_params_preset(ctypes.byref(p), PROFILES.get(profile, profile) if isinstance(profile, str) else profile)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise SkmmseError(status, where)
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Context:
+    """Owns the library's device scratch for calls ordered on one stream."""
+
+    def __init__(self):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.skmmse_create(ctypes.byref(h)), "skmmse_create")
+        self._h = h
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.skmmse_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------------------------
+    def conceal(self, frame, mb_lost, p: Params | None = None, *, out=None, out_f32=None,
+                stats: bool = False, stream=None):
+        """frame: uint8 CUDA tensor [H, W]; mb_lost: uint8 CUDA tensor [ceil(H/16), ceil(W/16)].
+        Returns (out, out_f32, stats_dict_or_None); out_f32 only if given (or True)."""
+        import torch
+        p = p if p is not None else params()
+        assert frame.is_cuda and frame.dtype == torch.uint8 and frame.dim() == 2
+        assert mb_lost.is_cuda and mb_lost.dtype == torch.uint8 and mb_lost.is_contiguous()
+        H, W = frame.shape
+        if out is None:
+            out = torch.empty_like(frame)
+        if out_f32 is True:
+            out_f32 = torch.zeros((H, W), dtype=torch.float32, device=frame.device)
+        st = Stats() if stats else None
+        rc = self._lib.skmmse_conceal(
+            self._h, frame.data_ptr(), W, H, frame.stride(0), mb_lost.data_ptr(), ctypes.byref(p),
+            out.data_ptr(), out.stride(0), out_f32.data_ptr() if out_f32 is not None else None,
+            ctypes.byref(st) if st is not None else None, _stream_handle(stream))
+        _check(rc, "skmmse_conceal")
+        return out, out_f32, (st.as_dict() if st is not None else None)
+
+    def conceal_batch(self, frames, masks, p: Params | None = None, *, outs=None, outs_f32=None,
+                      traces=None, stats: bool = False, stream=None):
+        """Batch of frames (lists of uint8 CUDA tensors); one persistent launch."""
+        import torch
+        p = p if p is not None else params()
+        n = len(frames)
+        if outs is None:
+            outs = [torch.empty_like(f) for f in frames]
+        descs = (Frame * n)()
+        for i, (f, m) in enumerate(zip(frames, masks)):
+            H, W = f.shape
+            d = descs[i]
+            d.frame, d.width, d.height, d.pitch = f.data_ptr(), W, H, f.stride(0)
+            d.mb_lost = m.data_ptr()
+            d.out, d.out_pitch = outs[i].data_ptr(), outs[i].stride(0)
+            if outs_f32 is not None and outs_f32[i] is not None:
+                d.out_f32, d.out_f32_pitch = outs_f32[i].data_ptr(), outs_f32[i].stride(0)
+            if traces is not None and traces[i] is not None:
+                d.trace = traces[i].data_ptr()
+        st = Stats() if stats else None
+        rc = self._lib.skmmse_conceal_batch(self._h, descs, n, ctypes.byref(p),
+                                            ctypes.byref(st) if st is not None else None,
+                                            _stream_handle(stream))
+        _check(rc, "skmmse_conceal_batch")
+        return outs, (st.as_dict() if st is not None else None)
+
+    def read_stats(self, stream=None) -> dict:
+        st = Stats()
+        rc = self._lib.skmmse_read_stats(self._h, ctypes.byref(st), _stream_handle(stream))
+        d = st.as_dict()
+        d["status"] = rc
+        return d
+
+
+def trace_buffer(mb_lost_np: np.ndarray, device="cuda"):
+    """Device buffer for the per-patch decision records of one frame."""
+    import torch
+    nlost = int((np.asarray(mb_lost_np) != 0).sum())
+    return torch.zeros(max(1, nlost) * 64 * TRACE_DTYPE.itemsize, dtype=torch.uint8, device=device)
+
+
+def trace_to_numpy(buf, nlost: int) -> np.ndarray:
+    raw = buf.cpu().numpy().tobytes()
+    return np.frombuffer(raw, dtype=TRACE_DTYPE).reshape(max(1, nlost), 64)[:nlost]
+
+
+def conceal_numpy(frame: np.ndarray, mb_lost: np.ndarray, p: Params | None = None, *,
+                  trace: bool = False, ctx: Context | None = None, force_x: np.ndarray | None = None):
+    """Host-buffer convenience: copy in, conceal on cuda:0, copy out.
+    Returns dict(out=uint8 [H, W], out_f32=float32 [H, W], stats, trace).
+    force_x (verification hook, float [n_lost, 64, 4]): reference estimates written back
+    into the support after each step instead of the kernel's own (SKMMSE_FLAG_FORCE)."""
+    import torch
+    p = params() if p is None else p
+    ctx = ctx or Context()
+    f = torch.from_numpy(np.ascontiguousarray(frame, dtype=np.uint8)).cuda()
+    m = torch.from_numpy(np.ascontiguousarray(mb_lost, dtype=np.uint8)).cuda()
+    of = torch.zeros(f.shape, dtype=torch.float32, device=f.device)
+    tb = None
+    if trace or force_x is not None:
+        p = Params.from_buffer_copy(p)
+        p.flags |= FLAG_TRACE
+        nlost = int((np.asarray(mb_lost) != 0).sum())
+        if force_x is not None:
+            p.flags |= FLAG_FORCE
+            rec = np.zeros((max(1, nlost), 64), dtype=TRACE_DTYPE)
+            rec["x"][:nlost] = np.asarray(force_x, dtype=np.float32).reshape(nlost, 64, 4)
+            tb = torch.from_numpy(rec.view(np.uint8).reshape(-1).copy()).cuda()
+        else:
+            tb = trace_buffer(mb_lost)
+    outs, st = ctx.conceal_batch([f], [m], p, outs_f32=[of], traces=[tb] if tb is not None else None,
+                                 stats=True)
+    torch.cuda.synchronize()
+    nlost = int((mb_lost != 0).sum())
+    return {"out": outs[0].cpu().numpy(), "out_f32": of.cpu().numpy(), "stats": st,
+            "trace": trace_to_numpy(tb, nlost) if tb is not None else None}

@@ -1,0 +1,145 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same
+seeded inputs, element by element.  Each configuration runs
+
+  - teacher-forced: every step of the kernel starts from exactly the oracle's inputs
+    (binary32-stored oracle estimates written back), every estimate within 1e-3 gray;
+  - free-running: both run independently; decisions and values agree up to the first
+    near-tie of each block, and the whole-frame PSNR agrees within 0.01 dB.
+
+Sizes span many candidate chunks, several work-queue entries, ragged frame edges and
+dependency chains (see tests/parity.py for the comparison rules)."""
+import numpy as np
+import pytest
+
+from paper_2205_11226_gb300 import skmmse, synth
+
+from parity import compare, free_running_summary, run_forced, run_pair
+
+pytestmark = pytest.mark.gpu
+
+FREE_TOL = 0.25      # free-running: bound on |gpu - oracle| before the first decision flip
+PSNR_TOL = 0.01      # dB
+
+
+def check(frame, m, p, ctx, free=True):
+    gpu, orc = run_forced(frame, m, p, ctx)
+    rep = compare(frame, m, gpu, orc, p, forced=True)
+    assert rep["compared"] + rep["flips"] == rep["patches"], rep
+    assert rep["flips"] <= max(2, rep["patches"] // 200), rep
+    if free:
+        g2, o2 = run_pair(frame, m, p, ctx)
+        rep2 = compare(frame, m, g2, o2, p, tol=FREE_TOL)
+        s = free_running_summary(frame, m, g2, o2)
+        assert abs(s["psnr_gpu"] - s["psnr_oracle"]) <= PSNR_TOL, s
+        rep["free"] = {**s, "compared": rep2["compared"], "patches": rep2["patches"],
+                       "flips": rep2["flips"]}
+    return rep, gpu, orc
+
+
+@pytest.mark.parametrize("profile", ["express", "efficient", "excellent"])
+def test_single_block_256(gpu_ctx, profile):
+    f, m = synth.workload_single(0)
+    rep, gpu, orc = check(f, m, skmmse.params(profile), gpu_ctx)
+    assert gpu["stats"]["n_patches"] == 64 and gpu["stats"]["n_lost_mbs"] == 1
+    assert rep["compared"] == 64
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_forced_hql_single_block(gpu_ctx, seed):
+    # every patch through HQL: covariance, factorisation, beta grid, I0, alpha
+    f, m = synth.workload_single(seed)
+    p = skmmse.params("efficient", t_phi=-1.0, t_nu=1e30)
+    rep, gpu, orc = check(f, m, p, gpu_ctx)
+    assert gpu["stats"]["n_hql"] == 64
+
+
+def test_forced_idl_single_block(gpu_ctx):
+    f, m = synth.workload_single(3)
+    p = skmmse.params("efficient", t_phi=-1.0, t_nu=1e-6)
+    rep, gpu, orc = check(f, m, p, gpu_ctx)
+    assert gpu["stats"]["n_idl"] == 64
+
+
+@pytest.mark.parametrize("profile", ["efficient", "excellent"])
+def test_checkerboard_ragged(gpu_ctx, profile):
+    # 200 x 120: partial block column (8 px) and row (8 px); isolated losses
+    f = synth.make_frame(200, 120, 7)
+    m = synth.loss_checkerboard(200, 120)
+    m[7, 12] = 1  # a partial corner block
+    check(f, m, skmmse.params(profile), gpu_ctx)
+
+
+def test_slice_chains(gpu_ctx):
+    # consecutive losses: blocks depend on concealed neighbours (raster order)
+    f = synth.make_frame(256, 160, 8, fine_texture=True)
+    m = synth.loss_runs(256, 160, 3, 0.25)
+    check(f, m, skmmse.params("efficient"), gpu_ctx)
+
+
+def test_received_only_support(gpu_ctx):
+    f = synth.make_frame(256, 160, 9)
+    m = synth.loss_runs(256, 160, 4, 0.25)
+    check(f, m, skmmse.params("efficient", concealed_is_support=0), gpu_ctx)
+
+
+def test_constant_and_fully_lost(gpu_ctx):
+    f = np.full((64, 96), 77, np.uint8)
+    m = np.zeros((4, 6), np.uint8)
+    m[1:3, 1:5] = 1
+    g = skmmse.conceal_numpy(f, m, skmmse.params("excellent"), ctx=gpu_ctx)
+    assert np.all(g["out"] == 77) and np.all(np.abs(g["out_f32"][16:48, 16:80] - 77) < 1e-5)
+    f = synth.make_frame(48, 32, 2)
+    m = np.ones((2, 3), np.uint8)
+    g = skmmse.conceal_numpy(f, m, skmmse.params("efficient"), ctx=gpu_ctx)
+    assert np.all(g["out"] == 128)
+
+
+def test_batch_equals_single_calls(gpu_ctx):
+    import torch
+    frames, masks = synth.workload_batch(5, sizes=[(352, 288), (128, 96), (200, 120)])
+    p = skmmse.params("efficient")
+    alone = [skmmse.conceal_numpy(f, m, p, ctx=gpu_ctx)["out_f32"] for f, m in zip(frames, masks)]
+    fd = [torch.from_numpy(f).cuda() for f in frames]
+    md = [torch.from_numpy(m).cuda() for m in masks]
+    of = [torch.zeros(f.shape, dtype=torch.float32, device="cuda") for f in frames]
+    outs, st = gpu_ctx.conceal_batch(fd, md, p, outs_f32=of, stats=True)
+    torch.cuda.synchronize()
+    for a, b in zip(alone, of):
+        assert np.array_equal(a, b.cpu().numpy())
+    assert st["n_lost_mbs"] == sum(int(m.sum()) for m in masks)
+
+
+def test_in_place_and_trace_off_identical(gpu_ctx):
+    import torch
+    f, m = synth.workload_checkerboard(6, 128, 128)
+    p = skmmse.params("efficient")
+    ref = skmmse.conceal_numpy(f, m, p, trace=True, ctx=gpu_ctx)["out"]
+    fd = torch.from_numpy(f).cuda()
+    md = torch.from_numpy(m).cuda()
+    gpu_ctx.conceal(fd, md, p, out=fd)
+    torch.cuda.synchronize()
+    assert np.array_equal(fd.cpu().numpy(), ref)
+
+
+def test_argument_errors(gpu_ctx):
+    import torch
+    f = torch.zeros((33, 32), dtype=torch.uint8, device="cuda")
+    m = torch.zeros((3, 2), dtype=torch.uint8, device="cuda")
+    with pytest.raises(skmmse.SkmmseError) as e:
+        gpu_ctx.conceal(f, m)
+    assert e.value.status == 2
+    f = torch.zeros((32, 32), dtype=torch.uint8, device="cuda")
+    m = torch.zeros((2, 2), dtype=torch.uint8, device="cuda")
+    with pytest.raises(skmmse.SkmmseError) as e:
+        gpu_ctx.conceal(f, m, skmmse.params("efficient", t_nu=0.0))
+    assert e.value.status == 1
+    with pytest.raises(skmmse.SkmmseError) as e:
+        gpu_ctx.conceal(f, m, skmmse.params("efficient", beta_kmin=0, beta_kmax=40))
+    assert e.value.status == 1
+    with pytest.raises(skmmse.SkmmseError) as e:
+        gpu_ctx.conceal(f, m, skmmse.params("efficient", flags=skmmse.FLAG_FORCE))
+    assert e.value.status == 1
+    # nothing lost: output equals input
+    g = torch.randint(0, 255, (32, 32), dtype=torch.uint8, device="cuda")
+    out, _, st = gpu_ctx.conceal(g, m, stats=True)
+    assert torch.equal(out, g) and st["n_lost_mbs"] == 0

@@ -1,0 +1,65 @@
+"""CPU-side checks of the C-ABI library: it builds for sm_103a, loads, exports every
+entry point include/skmmse.h declares, and its struct layouts and presets agree with the
+binding and with Table I.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2205_11226_gb300 import build, skmmse
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return skmmse.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "skmmse.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(skmmse_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert set(names) == set(skmmse.EXPORTS), names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_struct_layouts(lib):
+    assert lib.skmmse_abi_version() == 1
+    assert lib.skmmse_struct_size(0) == skmmse.TRACE_DTYPE.itemsize == 120
+    assert lib.skmmse_struct_size(1) == ctypes.sizeof(skmmse.Stats)
+    assert lib.skmmse_struct_size(2) == ctypes.sizeof(skmmse.Params)
+    assert lib.skmmse_struct_size(3) == ctypes.sizeof(skmmse.Frame)
+    assert lib.skmmse_struct_size(9) == -1
+
+
+def test_presets_follow_table1(lib):
+    rows = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "table1_profiles.txt")):
+        line = line.split("#")[0].split()
+        if line:
+            rows[line[0]] = [float(v) for v in line[1:]]
+    for name, code in skmmse.PROFILES.items():
+        p = skmmse.params(code)
+        assert p.t_phi == rows[name][0]
+        assert p.t_nu == pytest.approx(rows[name][1], rel=1e-6)
+        assert p.sigma2 == rows["sigma2"][0]
+        assert (p.ring_step, p.beta_kmin, p.beta_kmax, p.concealed_is_support) == (4, -8, 16, 1)
+
+
+def test_null_arguments_rejected_without_compute(lib):
+    p = skmmse.params()
+    f = skmmse.Frame()
+    assert lib.skmmse_conceal_batch(None, ctypes.byref(f), 1, ctypes.byref(p), None, None) == 1
+    assert lib.skmmse_create(None) == 1
+    assert lib.skmmse_read_stats(None, None, None) == 1
+    lib.skmmse_destroy(None)
+    assert lib.skmmse_status_str(6) == b"dependency wait timed out on the device"
+    assert lib.skmmse_status_str(99) == b"unknown status"

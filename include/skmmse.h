@@ -188,6 +188,13 @@ skmmse_status skmmse_conceal_batch(skmmse_context* ctx, const skmmse_frame* h_fr
    Returns SKMMSE_ERR_TIMEOUT if a dependency wait gave up during that call. */
 skmmse_status skmmse_read_stats(skmmse_context* ctx, skmmse_stats* h_stats, void* stream);
 
+/* Diagnostic: per-phase SM clock cycles of the context's last call, summed over CTAs
+   (thread 0's view, barrier waits included): 0 staging, 1 patch selection and context,
+   2 BRL, 3 IDL, 4 HQL candidate list, 5 covariance, 6 factorisation, 7 distances,
+   8 beta grid, 9 I0, 10 leave-one-out pass, 11 HQL estimate, 12 write-back, 13 publish.
+   All zero unless the library was built with -DSKMMSE_PHASE_CLOCKS.  Synchronises. */
+skmmse_status skmmse_read_phase_clocks(skmmse_context* ctx, long long* h_clocks16, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

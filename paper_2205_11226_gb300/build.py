@@ -14,7 +14,10 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-LIB = os.path.join(PKG, "libskmmse.so")
+# SKMMSE_PHASE_CLOCKS=1 in the environment selects the phase-clock diagnostic variant,
+# built into its own file so that it never stands in for the release library
+PHASE_CLOCKS = os.environ.get("SKMMSE_PHASE_CLOCKS", "0") == "1"
+LIB = os.path.join(PKG, "libskmmse_phase.so" if PHASE_CLOCKS else "libskmmse.so")
 SOURCES = [os.path.join(CSRC, "skmmse_api.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(INCLUDE, "skmmse.h")]
@@ -43,6 +46,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         tmp = LIB + f".{os.getpid()}.tmp"
         cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-I" + INCLUDE,
                "-Xcompiler", "-fPIC", "-shared", "-o", tmp] + SOURCES
+        if PHASE_CLOCKS:
+            cmd.insert(1, "-DSKMMSE_PHASE_CLOCKS")
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -353,4 +353,14 @@ skmmse_status skmmse_read_stats(skmmse_context* c, skmmse_stats* h, void* stream
     return counters[2] ? SKMMSE_ERR_TIMEOUT : SKMMSE_OK;
 }
 
+skmmse_status skmmse_read_phase_clocks(skmmse_context* c, long long* h_clocks16, void* stream_v) {
+    if (!c || !h_clocks16) return SKMMSE_ERR_ARG;
+    unsigned long long raw[sk::kNPhase];
+    SK_CHECK(cudaMemcpyAsync(raw, c->d_stats + sk::kPhaseBase, sizeof(raw), cudaMemcpyDeviceToHost,
+                             static_cast<cudaStream_t>(stream_v)));
+    SK_CHECK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream_v)));
+    for (int i = 0; i < sk::kNPhase; ++i) h_clocks16[i] = (long long)raw[i];
+    return SKMMSE_OK;
+}
+
 }  // extern "C"

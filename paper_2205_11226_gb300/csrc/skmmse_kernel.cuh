@@ -39,7 +39,9 @@ constexpr int kCh = 64;          // HQL candidate chunk
 constexpr int kZs = 40;          // staged row: x'(4) y'(32) one(1) pad(3)
 constexpr int kMaxBeta = 32;
 constexpr int kMaxI0 = 33;
-constexpr int kNStats = 32;
+constexpr int kNStats = 64;
+constexpr int kPhaseBase = 32;  // stats slots 32..47: phase clocks (SKMMSE_PHASE_CLOCKS builds)
+constexpr int kNPhase = 16;
 
 // stats slots (match skmmse_stats field order)
 enum {
@@ -51,6 +53,28 @@ enum {
 static_assert(ST_COUNT <= kNStats, "stats slots");
 
 enum { L_EMPTY = 0, L_BRL = 1, L_IDL = 2, L_HQL = 3, L_NOCAND = 4 };
+
+// Phase clocks: thread 0 of each CTA adds the SM clock cycles spent since its previous
+// mark to the slot of the phase that just ended (barrier waits included).  Compiled in
+// only with -DSKMMSE_PHASE_CLOCKS; the release build keeps the slots at zero.
+enum {
+    PH_STAGE = 0, PH_CTX, PH_BRL, PH_IDL, PH_H0, PH_H1, PH_CHOL, PH_H2, PH_H3, PH_H4, PH_H5,
+    PH_HFIN, PH_WB, PH_PUB
+};
+#ifdef SKMMSE_PHASE_CLOCKS
+#define SK_PHASE(slot)                                           \
+    do {                                                         \
+        if (threadIdx.x == 0) {                                  \
+            const long long t_ = clock64();                      \
+            sm.st[kPhaseBase + (slot)] += (unsigned long long)(t_ - sm.ph_t); \
+            sm.ph_t = t_;                                        \
+        }                                                        \
+    } while (0)
+#else
+#define SK_PHASE(slot) \
+    do {               \
+    } while (0)
+#endif
 
 struct KParams {
     float t_phi;
@@ -170,6 +194,7 @@ struct __align__(128) Smem {
     int pad0;
     unsigned long long st[kNStats];    // per-CTA counters
     TraceRec tr;                       // trace record of the current step
+    long long ph_t;                    // last phase mark (SKMMSE_PHASE_CLOCKS)
     union {
         IdlSlot idl[2][kWarps];
         Hql hql;
@@ -517,6 +542,7 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
     }
     __syncthreads();
     const int M = h.M;
+    SK_PHASE(PH_H0);
 
     // H1: mean and covariance of z' = z - shift, Eq. (8).  Integer parts accumulate
     // exactly (|n'| <= 255, at most kCh products per thread per chunk < 2^24), the
@@ -613,6 +639,7 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
         h.colF[tid - 220] = colF;
     }
     __syncthreads();
+    SK_PHASE(PH_H1);
 
     // finalise C_ab = S_ab/M - T_a T_b / M^2 in double-float; YY (+ridge later), XY
     {
@@ -715,6 +742,7 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
         h.K[a][j] = kk;
     }
 
+    SK_PHASE(PH_CHOL);
     // H2: whitened distances d_j = ||L^-1 (y_j - y0)||^2 (Mahalanobis, Eq. (6) with C_YY)
     // thread tile: 2 candidates x 4 whitened coordinates
     const int tj = (tid >> 3) * 2, tq = tid & 7;
@@ -789,6 +817,7 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
     }
     __syncthreads();
     const float dmin = h.dmin;
+    SK_PHASE(PH_H2);
 
     // H3: beta grid, Eqs. (9)-(10): accB[b][k] = sum_j w_j(b) z'_j[k], column 36 = sum w
     const int nb = P.nbeta;
@@ -903,6 +932,7 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
         }
     }
 
+    SK_PHASE(PH_H3);
     // H4: I0 = the n0 smallest d_j, ties to the lower index (radix select on the bits)
     int n0 = min(ny + 1, M - 1);
     if (n0 < 0) n0 = 0;
@@ -979,6 +1009,7 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
     }
     __syncthreads();
 
+    SK_PHASE(PH_H4);
     // H5: leave-one-out predictions for i in I0 at beta* (Eqs. (11)-(12))
     float num = 0.0f, den = 0.0f;
     if (n0 > 0) {
@@ -1093,6 +1124,7 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
             }
         }
     }
+    SK_PHASE(PH_H5);
     num = warp_sum(num);
     den = warp_sum(den);
     __syncthreads();
@@ -1139,6 +1171,13 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
         sm.st[ST_HQL_M] += M;
         sm.st[ST_HQL_MNY] += (unsigned long long)M * ny;
         sm.st[ST_HQL_I0M] += (unsigned long long)n0 * M;
+#ifdef SKMMSE_PHASE_CLOCKS
+        {
+            const long long t_ = clock64();
+            sm.st[kPhaseBase + PH_HFIN] += (unsigned long long)(t_ - sm.ph_t);
+            sm.ph_t = t_;
+        }
+#endif
         // algorithmic FP32 operations of this HQL estimate (one exp counts as one):
         // covariance (upper C_YY and C_XY), two whitening passes with the distance,
         // beta grid (exp + weighted sums of 4+Ny+1 columns), leave-one-out pass
@@ -1169,6 +1208,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(WorkDev W, KParams
     __syncthreads();
     unsigned phase = 0;
     const int n_entries = W.counters[0];
+    if (tid == 0) sm.ph_t = clock64();
 
     for (;;) {
         if (tid == 0) sm.entry = atomicAdd(&W.counters[1], 1);
@@ -1263,6 +1303,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(WorkDev W, KParams
         }
         __syncthreads();
 
+        SK_PHASE(PH_STAGE);
         TraceRec* trace_base =
             (trace_on && F.trace) ? reinterpret_cast<TraceRec*>(F.trace) + (size_t)ent.z * 64 : nullptr;
         const int npatch = __popcll(sm.unfilled);
@@ -1315,6 +1356,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(WorkDev W, KParams
             c.phi = mx - mn;
             c.mean = c.ny > 0 ? sum / (float)c.ny : 0.0f;
 
+            SK_PHASE(PH_CTX);
             float xhat[4];
             int layer;
             int ring = 0;
@@ -1336,6 +1378,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(WorkDev W, KParams
                 xhat[0] = xhat[1] = xhat[2] = xhat[3] = c.mean;
             } else {
                 const int r = idl_step(sm, P, c, xhat, &ring, &lognu, &evals);
+                SK_PHASE(PH_IDL);
                 if (tid == 0) {
                     sm.st[ST_IDL_EVALS] += evals;
                     sm.st[ST_IDL_NY] += evals * c.ny;
@@ -1353,6 +1396,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(WorkDev W, KParams
                     hql_step(sm, P, c, xhat, &sm.tr, trace_base != nullptr);
                 }
             }
+            if (layer == L_EMPTY || layer == L_BRL) SK_PHASE(PH_BRL);
             // R8: clip and write back
             if (tid == 0) {
                 const int pr = c.wr + 2, pc = c.wc + 2;
@@ -1390,6 +1434,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(WorkDev W, KParams
                 }
             }
             __syncthreads();
+            SK_PHASE(PH_WB);
         }
 
         // publish: unrounded values for dependants, rounded / FP32 outputs
@@ -1406,9 +1451,10 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(WorkDev W, KParams
         __threadfence();
         __syncthreads();
         if (tid == 0) st_release(&W.done[e], 1u);
+        SK_PHASE(PH_PUB);
     }
     __syncthreads();
-    for (int i = tid; i < ST_COUNT; i += kThreads)
+    for (int i = tid; i < kNStats; i += kThreads)
         if (sm.st[i]) atomicAdd(&W.stats[i], sm.st[i]);
 }
 

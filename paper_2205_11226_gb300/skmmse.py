@@ -13,7 +13,8 @@ from dataclasses import dataclass
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libskmmse.so")
+LIB_PATH = os.path.join(_PKG, "libskmmse_phase.so" if os.environ.get("SKMMSE_PHASE_CLOCKS", "0") == "1"
+                        else "libskmmse.so")
 
 EXPRESS, EFFICIENT, EXCELLENT = 0, 1, 2
 PROFILES = {"express": EXPRESS, "efficient": EFFICIENT, "excellent": EXCELLENT}
@@ -69,7 +70,7 @@ TRACE_DTYPE = np.dtype([
 # every symbol include/skmmse.h declares
 EXPORTS = ["skmmse_abi_version", "skmmse_struct_size", "skmmse_status_str", "skmmse_params_preset",
            "skmmse_create", "skmmse_destroy", "skmmse_conceal", "skmmse_conceal_batch",
-           "skmmse_read_stats"]
+           "skmmse_read_stats", "skmmse_read_phase_clocks"]
 
 _lib = None
 
@@ -108,6 +109,8 @@ def load(path: str = LIB_PATH):
                                          ctypes.POINTER(Stats), vp]
     lib.skmmse_read_stats.restype = ci
     lib.skmmse_read_stats.argtypes = [vp, ctypes.POINTER(Stats), vp]
+    lib.skmmse_read_phase_clocks.restype = ci
+    lib.skmmse_read_phase_clocks.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), vp]
     assert lib.skmmse_struct_size(0) == TRACE_DTYPE.itemsize, "trace record layout"
     assert lib.skmmse_struct_size(1) == ctypes.sizeof(Stats), "stats layout"
     assert lib.skmmse_struct_size(2) == ctypes.sizeof(Params), "params layout"
@@ -204,6 +207,16 @@ class Context:
                                             _stream_handle(stream))
         _check(rc, "skmmse_conceal_batch")
         return outs, (st.as_dict() if st is not None else None)
+
+    PHASES = ["stage", "ctx", "brl", "idl", "h_cand", "h_cov", "h_chol", "h_dist", "h_beta",
+              "h_i0", "h_alpha", "h_est", "writeback", "publish"]
+
+    def read_phase_clocks(self, stream=None) -> dict:
+        """Per-phase SM cycles of the last call (library built with SKMMSE_PHASE_CLOCKS)."""
+        buf = (ctypes.c_longlong * 16)()
+        _check(self._lib.skmmse_read_phase_clocks(self._h, buf, _stream_handle(stream)),
+               "skmmse_read_phase_clocks")
+        return dict(zip(self.PHASES, list(buf)))
 
     def read_stats(self, stream=None) -> dict:
         st = Stats()

@@ -55,7 +55,9 @@ typedef enum {
     SKMMSE_ERR_NOMEM = 4,       /* scratch allocation failed */
     SKMMSE_ERR_CUDA = 5,        /* a CUDA runtime call failed */
     SKMMSE_ERR_TIMEOUT = 6,     /* a block's dependency wait gave up (device error word) */
-    SKMMSE_ERR_UNSUPPORTED = 7  /* requested precision or flag not built */
+    SKMMSE_ERR_UNSUPPORTED = 7, /* requested precision or flag not built */
+    SKMMSE_ERR_TOO_LARGE = 8    /* frame larger than the static scratch of
+                                   skmmse_conceal_noalloc (SKMMSE_NOALLOC_MAX_MBS blocks) */
 } skmmse_status;
 
 /* Arithmetic of the distance contraction.  FP32: every step in FP32 on the CUDA cores
@@ -187,6 +189,29 @@ skmmse_status skmmse_conceal_batch(skmmse_context* ctx, const skmmse_frame* h_fr
 /* Synchronise `stream` and copy the counters of the context's last call into *h_stats.
    Returns SKMMSE_ERR_TIMEOUT if a dependency wait gave up during that call. */
 skmmse_status skmmse_read_stats(skmmse_context* ctx, skmmse_stats* h_stats, void* stream);
+
+/* Largest frame, in 16x16 blocks (partial edge blocks included), that
+   skmmse_conceal_noalloc accepts: 8192 covers 1920x1080 (120 x 68 = 8160 blocks). */
+#define SKMMSE_NOALLOC_MAX_MBS 8192
+
+/* skmmse_conceal_noalloc: the same concealment as skmmse_conceal for one frame, for callers
+   that cannot allocate device memory -- for example code running inside a memory pool or
+   an allocator hook, under a strict device-memory budget, or anywhere a cudaMalloc would
+   synchronise or fail.  The paper has no counterpart; this is an interface convenience.
+   It calls no cudaMalloc, cudaFree, cudaMallocHost or allocating library routine.  Its
+   scratch (work queue, dependency flags, per-block values, counters) is one static device
+   array of about 8.6 MB, sized for SKMMSE_NOALLOC_MAX_MBS blocks; every GPU that loads the
+   library holds it until the process exits.  Larger frames return SKMMSE_ERR_TOO_LARGE.
+   The first call on a device looks up the array's device address and sets kernel
+   attributes for that device (make it before any stream capture on that device).  All
+   calls share the one array and it keeps the last call's contents: calls that may overlap
+   on the GPU (different streams, or host threads without ordering) race; order them on one
+   stream.  Arguments as skmmse_conceal; p->flags must be 0 (no trace).  h_stats (nullable)
+   makes the call synchronous and returns the counters. */
+skmmse_status skmmse_conceal_noalloc(const uint8_t* d_frame, int width, int height, int pitch,
+                                     const uint8_t* d_mb_lost, const skmmse_params* p,
+                                     uint8_t* d_out, int out_pitch, float* d_out_f32,
+                                     skmmse_stats* h_stats, void* stream);
 
 /* Diagnostic: per-phase SM clock cycles of the context's last call, summed over CTAs
    (thread 0's view, barrier waits included): 0 staging, 1 patch selection and context,

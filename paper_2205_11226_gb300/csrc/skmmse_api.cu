@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -42,7 +43,7 @@ struct skmmse_context {
 
 namespace {
 
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 skmmse_status cuda_fail(cudaError_t e) {
     (void)cudaGetLastError();
@@ -106,6 +107,81 @@ KParams make_kparams(const skmmse_params* p) {
     return k;
 }
 
+// ------------------------------------------------------------------------------------
+// Scratch for skmmse_conceal_noalloc(): one file-scope device array, sized for frames of up
+// to SKMMSE_NOALLOC_MAX_MBS blocks.  Every GPU that loads the library holds it until the
+// process exits.  Layout (byte offsets, each 256-aligned): frame descriptor, tensor map,
+// counters + stats, entry_of_mb, entries, done flags, per-block values.
+constexpr size_t kNaMax = SKMMSE_NOALLOC_MAX_MBS;
+constexpr size_t kNaFrame = 0;
+constexpr size_t kNaTmap = 256;
+constexpr size_t kNaCounters = 512;
+constexpr size_t kNaStats = 768;
+constexpr size_t kNaEom = align_up(kNaStats + sizeof(unsigned long long) * sk::kNStats, 256);
+constexpr size_t kNaEnt = align_up(kNaEom + sizeof(int) * kNaMax, 256);
+constexpr size_t kNaDone = align_up(kNaEnt + sizeof(int4) * kNaMax, 256);
+constexpr size_t kNaVals = align_up(kNaDone + sizeof(unsigned) * kNaMax, 256);
+constexpr size_t kNaBytes = align_up(kNaVals + sizeof(float) * 256 * kNaMax, 256);
+static_assert(sizeof(FrameDev) <= 256 && sizeof(CUtensorMap) <= 256, "scratch header");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+// Writes the frame descriptor and tensor map (passed by value) into the scratch and clears
+// what must start at zero: the queue counters and the statistics.
+__global__ void noalloc_setup_kernel(FrameDev fd, CUtensorMap tm, unsigned char* scratch) {
+    if (threadIdx.x == 0) {
+        *reinterpret_cast<FrameDev*>(scratch + kNaFrame) = fd;
+        *reinterpret_cast<CUtensorMap*>(scratch + kNaTmap) = tm;
+    }
+    int* counters = reinterpret_cast<int*>(scratch + kNaCounters);
+    unsigned long long* stats = reinterpret_cast<unsigned long long*>(scratch + kNaStats);
+    if (threadIdx.x < 4) counters[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < sk::kNStats; i += blockDim.x) stats[i] = 0ull;
+}
+
+struct NoAllocDevice {
+    bool ready = false;
+    unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch on this device
+    int sm_count = 0;
+    int blocks_per_sm = 0;
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+};
+constexpr int kNaMaxDevices = 64;
+NoAllocDevice g_na_dev[kNaMaxDevices];
+std::mutex g_na_mu;
+
+// Once per device, with that device current: the device address of the scratch array
+// (the host-side symbol is only a stand-in), kernel attributes and occupancy.
+skmmse_status noalloc_setup(int dev, NoAllocDevice** out) {
+    if (dev < 0 || dev >= kNaMaxDevices) return SKMMSE_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_na_mu);
+    NoAllocDevice& d = g_na_dev[dev];
+    if (!d.ready) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || ptr == nullptr) return cuda_fail(e);
+        e = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(sk::conceal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(sk::Smem));
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, sk::conceal_kernel,
+                                                              sk::kThreads, sizeof(sk::Smem));
+        if (e != cudaSuccess || d.blocks_per_sm < 1) return cuda_fail(e);
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            d.encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        (void)cudaGetLastError();
+        d.scratch = static_cast<unsigned char*>(ptr);
+        d.ready = true;
+    }
+    *out = &d;
+    return SKMMSE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -132,6 +208,8 @@ const char* skmmse_status_str(skmmse_status s) {
         case SKMMSE_ERR_CUDA: return "CUDA runtime error";
         case SKMMSE_ERR_TIMEOUT: return "dependency wait timed out on the device";
         case SKMMSE_ERR_UNSUPPORTED: return "unsupported precision or flag";
+        case SKMMSE_ERR_TOO_LARGE:
+            return "frame exceeds the static scratch of skmmse_conceal_noalloc (SKMMSE_NOALLOC_MAX_MBS blocks)";
         default: return "unknown status";
     }
 }
@@ -351,6 +429,103 @@ skmmse_status skmmse_read_stats(skmmse_context* c, skmmse_stats* h, void* stream
     h->n_beta = c->last_nbeta;
     h->error = counters[2];
     return counters[2] ? SKMMSE_ERR_TIMEOUT : SKMMSE_OK;
+}
+
+skmmse_status skmmse_conceal_noalloc(const uint8_t* d_frame, int width, int height, int pitch,
+                                     const uint8_t* d_mb_lost, const skmmse_params* p,
+                                     uint8_t* d_out, int out_pitch, float* d_out_f32,
+                                     skmmse_stats* h_stats, void* stream_v) {
+    skmmse_frame f;
+    std::memset(&f, 0, sizeof(f));
+    f.frame = d_frame;
+    f.width = width;
+    f.height = height;
+    f.pitch = pitch;
+    f.mb_lost = d_mb_lost;
+    f.out = d_out;
+    f.out_pitch = out_pitch;
+    f.out_f32 = d_out_f32;
+    f.out_f32_pitch = width;
+    skmmse_status s = validate_params(p);
+    if (s != SKMMSE_OK) return s;
+    if (p->flags != 0) return SKMMSE_ERR_ARG;  // no trace buffer on this entry point
+    s = validate_frame(f);
+    if (s != SKMMSE_OK) return s;
+    const long long mbw = (width + 15) / 16, mbh = (height + 15) / 16;
+    if (mbw * mbh > (long long)kNaMax) return SKMMSE_ERR_TOO_LARGE;
+    int dev = 0;
+    SK_CHECK(cudaGetDevice(&dev));
+    NoAllocDevice* nd = nullptr;
+    s = noalloc_setup(dev, &nd);
+    if (s != SKMMSE_OK) return s;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+
+    FrameDev fd;
+    std::memset(&fd, 0, sizeof(fd));
+    fd.in = d_frame;
+    fd.out = d_out;
+    fd.out_f32 = d_out_f32;
+    fd.lost = d_mb_lost;
+    fd.trace = nullptr;
+    fd.w = width;
+    fd.h = height;
+    fd.pitch = pitch;
+    fd.out_pitch = out_pitch;
+    fd.out_f32_pitch = d_out_f32 ? width : 0;
+    fd.mbw = (int)mbw;
+    fd.mbh = (int)mbh;
+    fd.mb_base = 0;
+    CUtensorMap tm;
+    std::memset(&tm, 0, sizeof(tm));
+    const bool aligned = (reinterpret_cast<uintptr_t>(d_frame) % 16 == 0) && (pitch % 16 == 0);
+    if (nd->encode && aligned) {
+        cuuint64_t gdim[2] = {(cuuint64_t)width, (cuuint64_t)height};
+        cuuint64_t gstride[1] = {(cuuint64_t)pitch};
+        cuuint32_t box[2] = {(cuuint32_t)sk::kReg, (cuuint32_t)sk::kReg};
+        cuuint32_t estr[2] = {1, 1};
+        fd.use_tma = nd->encode(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(d_frame),
+                                gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    unsigned char* sc = nd->scratch;
+    if (d_out != d_frame)
+        SK_CHECK(cudaMemcpy2DAsync(d_out, out_pitch, d_frame, pitch, width, height,
+                                   cudaMemcpyDeviceToDevice, stream));
+    noalloc_setup_kernel<<<1, 64, 0, stream>>>(fd, tm, sc);
+    SK_CHECK(cudaGetLastError());
+    WorkDev w;
+    w.frames = reinterpret_cast<const FrameDev*>(sc + kNaFrame);
+    w.tmaps = reinterpret_cast<const CUtensorMap*>(sc + kNaTmap);
+    w.nframes = 1;
+    w.entry_of_mb = reinterpret_cast<int*>(sc + kNaEom);
+    w.entries = reinterpret_cast<int4*>(sc + kNaEnt);
+    w.counters = reinterpret_cast<int*>(sc + kNaCounters);
+    w.done = reinterpret_cast<unsigned*>(sc + kNaDone);
+    w.vals = reinterpret_cast<float*>(sc + kNaVals);
+    w.stats = reinterpret_cast<unsigned long long*>(sc + kNaStats);
+    const KParams kp = make_kparams(p);
+    sk::build_queue_kernel<<<1, sk::kThreads, 0, stream>>>(w);
+    SK_CHECK(cudaGetLastError());
+    long long grid = (long long)nd->sm_count * nd->blocks_per_sm;
+    if (grid > mbw * mbh) grid = mbw * mbh;
+    if (grid < 1) grid = 1;
+    sk::conceal_kernel<<<(unsigned)grid, sk::kThreads, sizeof(sk::Smem), stream>>>(w, kp);
+    SK_CHECK(cudaGetLastError());
+    if (h_stats) {
+        unsigned long long raw[sk::kNStats];
+        int counters[4];
+        SK_CHECK(cudaMemcpyAsync(raw, w.stats, sizeof(raw), cudaMemcpyDeviceToHost, stream));
+        SK_CHECK(cudaMemcpyAsync(counters, w.counters, sizeof(counters), cudaMemcpyDeviceToHost, stream));
+        SK_CHECK(cudaStreamSynchronize(stream));
+        std::memset(h_stats, 0, sizeof(*h_stats));
+        long long* dst = &h_stats->n_lost_mbs;
+        for (int i = 0; i < sk::ST_COUNT; ++i) dst[i] = (long long)raw[i];
+        h_stats->n_beta = kp.nbeta;
+        h_stats->error = counters[2];
+        if (counters[2]) return SKMMSE_ERR_TIMEOUT;
+    }
+    return SKMMSE_OK;
 }
 
 skmmse_status skmmse_read_phase_clocks(skmmse_context* c, long long* h_clocks16, void* stream_v) {

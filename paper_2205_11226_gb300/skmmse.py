@@ -24,7 +24,9 @@ FLAG_FORCE = 2
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported frame shape", 3: "unsupported alignment",
           4: "device memory allocation failed", 5: "CUDA runtime error",
-          6: "dependency wait timed out on the device", 7: "unsupported precision or flag"}
+          6: "dependency wait timed out on the device", 7: "unsupported precision or flag",
+          8: "frame exceeds the static scratch of the no-allocation entry point"}
+NOALLOC_MAX_MBS = 8192
 
 
 class Params(ctypes.Structure):
@@ -70,7 +72,7 @@ TRACE_DTYPE = np.dtype([
 # every symbol include/skmmse.h declares
 EXPORTS = ["skmmse_abi_version", "skmmse_struct_size", "skmmse_status_str", "skmmse_params_preset",
            "skmmse_create", "skmmse_destroy", "skmmse_conceal", "skmmse_conceal_batch",
-           "skmmse_read_stats", "skmmse_read_phase_clocks"]
+           "skmmse_read_stats", "skmmse_read_phase_clocks", "skmmse_conceal_noalloc"]
 
 _lib = None
 
@@ -109,6 +111,9 @@ def load(path: str = LIB_PATH):
                                          ctypes.POINTER(Stats), vp]
     lib.skmmse_read_stats.restype = ci
     lib.skmmse_read_stats.argtypes = [vp, ctypes.POINTER(Stats), vp]
+    lib.skmmse_conceal_noalloc.restype = ci
+    lib.skmmse_conceal_noalloc.argtypes = [vp, ci, ci, ci, vp, ctypes.POINTER(Params), vp, ci, vp,
+                                           ctypes.POINTER(Stats), vp]
     lib.skmmse_read_phase_clocks.restype = ci
     lib.skmmse_read_phase_clocks.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), vp]
     assert lib.skmmse_struct_size(0) == TRACE_DTYPE.itemsize, "trace record layout"

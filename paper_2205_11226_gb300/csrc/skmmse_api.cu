@@ -121,7 +121,9 @@ constexpr size_t kNaEom = align_up(kNaStats + sizeof(unsigned long long) * sk::k
 constexpr size_t kNaEnt = align_up(kNaEom + sizeof(int) * kNaMax, 256);
 constexpr size_t kNaDone = align_up(kNaEnt + sizeof(int4) * kNaMax, 256);
 constexpr size_t kNaVals = align_up(kNaDone + sizeof(unsigned) * kNaMax, 256);
-constexpr size_t kNaBytes = align_up(kNaVals + sizeof(float) * 256 * kNaMax, 256);
+constexpr size_t kNaLev = align_up(kNaVals + sizeof(float) * 256 * kNaMax, 256);
+constexpr size_t kNaHist = align_up(kNaLev + sizeof(int) * kNaMax, 256);  // hist + cursor
+constexpr size_t kNaBytes = align_up(kNaHist + sizeof(int) * 2 * kNaMax, 256);
 static_assert(sizeof(FrameDev) <= 256 && sizeof(CUtensorMap) <= 256, "scratch header");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
@@ -135,8 +137,10 @@ __global__ void noalloc_setup_kernel(FrameDev fd, CUtensorMap tm, unsigned char*
     }
     int* counters = reinterpret_cast<int*>(scratch + kNaCounters);
     unsigned long long* stats = reinterpret_cast<unsigned long long*>(scratch + kNaStats);
+    int* hist = reinterpret_cast<int*>(scratch + kNaHist);
     if (threadIdx.x < 4) counters[threadIdx.x] = 0;
     for (int i = threadIdx.x; i < sk::kNStats; i += blockDim.x) stats[i] = 0ull;
+    for (int i = threadIdx.x; i < 2 * (int)kNaMax; i += blockDim.x) hist[i] = 0;
 }
 
 struct NoAllocDevice {
@@ -282,12 +286,13 @@ skmmse_status skmmse_conceal_batch(skmmse_context* c, const skmmse_frame* frames
     if (n > 65536) return SKMMSE_ERR_SHAPE;
     skmmse_status s = validate_params(p);
     if (s != SKMMSE_OK) return s;
-    long long total_mbs = 0;
+    long long total_mbs = 0, max_mbs = 1;
     for (int i = 0; i < n; ++i) {
         s = validate_frame(frames[i]);
         if (s != SKMMSE_OK) return s;
         const long long mbw = (frames[i].width + 15) / 16, mbh = (frames[i].height + 15) / 16;
         total_mbs += mbw * mbh;
+        if (mbw * mbh > max_mbs) max_mbs = mbw * mbh;
     }
     if (total_mbs > (1ll << 28)) return SKMMSE_ERR_SHAPE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
@@ -300,6 +305,8 @@ skmmse_status skmmse_conceal_batch(skmmse_context* c, const skmmse_frame* frames
     const size_t o_ent = off; off = align_up(off + sizeof(int4) * total_mbs, 128);
     const size_t o_done = off; off = align_up(off + sizeof(unsigned) * total_mbs, 128);
     const size_t o_vals = off; off = align_up(off + sizeof(float) * 256 * total_mbs, 128);
+    const size_t o_lev = off; off = align_up(off + sizeof(int) * total_mbs, 128);
+    const size_t o_hist = off; off = align_up(off + sizeof(int) * 2 * max_mbs, 128);  // hist + cursor
     const size_t need = off;
     if (need > c->arena_bytes) {
         if (c->stage_pending) cudaEventSynchronize(c->stage_done);
@@ -372,6 +379,7 @@ skmmse_status skmmse_conceal_batch(skmmse_context* c, const skmmse_frame* frames
     c->stage_pending = true;
     SK_CHECK(cudaMemsetAsync(c->d_counters, 0, 4 * sizeof(int), stream));
     SK_CHECK(cudaMemsetAsync(c->d_stats, 0, sk::kNStats * sizeof(unsigned long long), stream));
+    SK_CHECK(cudaMemsetAsync(c->d_arena + o_hist, 0, sizeof(int) * 2 * max_mbs, stream));
 
     WorkDev w;
     w.frames = reinterpret_cast<const FrameDev*>(c->d_arena + o_frames);
@@ -383,10 +391,16 @@ skmmse_status skmmse_conceal_batch(skmmse_context* c, const skmmse_frame* frames
     w.done = reinterpret_cast<unsigned*>(c->d_arena + o_done);
     w.vals = reinterpret_cast<float*>(c->d_arena + o_vals);
     w.stats = c->d_stats;
+    w.level_of_mb = reinterpret_cast<int*>(c->d_arena + o_lev);
+    w.lvl_hist = reinterpret_cast<int*>(c->d_arena + o_hist);
+    w.lvl_cursor = w.lvl_hist + max_mbs;
+    w.nlev = (int)max_mbs;
     const KParams kp = make_kparams(p);
     c->last_nbeta = kp.nbeta;
 
-    sk::build_queue_kernel<<<n, sk::kThreads, 0, stream>>>(w);
+    sk::queue_levels_kernel<<<n, sk::kThreads, 0, stream>>>(w, kp.concealed_is_support);
+    sk::queue_offsets_kernel<<<1, sk::kThreads, 0, stream>>>(w);
+    sk::queue_fill_kernel<<<n, sk::kThreads, 0, stream>>>(w);
     SK_CHECK(cudaGetLastError());
     long long grid = (long long)c->sm_count * c->blocks_per_sm;
     if (grid > total_mbs) grid = total_mbs;
@@ -492,7 +506,7 @@ skmmse_status skmmse_conceal_noalloc(const uint8_t* d_frame, int width, int heig
     if (d_out != d_frame)
         SK_CHECK(cudaMemcpy2DAsync(d_out, out_pitch, d_frame, pitch, width, height,
                                    cudaMemcpyDeviceToDevice, stream));
-    noalloc_setup_kernel<<<1, 64, 0, stream>>>(fd, tm, sc);
+    noalloc_setup_kernel<<<1, sk::kThreads, 0, stream>>>(fd, tm, sc);
     SK_CHECK(cudaGetLastError());
     WorkDev w;
     w.frames = reinterpret_cast<const FrameDev*>(sc + kNaFrame);
@@ -504,8 +518,14 @@ skmmse_status skmmse_conceal_noalloc(const uint8_t* d_frame, int width, int heig
     w.done = reinterpret_cast<unsigned*>(sc + kNaDone);
     w.vals = reinterpret_cast<float*>(sc + kNaVals);
     w.stats = reinterpret_cast<unsigned long long*>(sc + kNaStats);
+    w.level_of_mb = reinterpret_cast<int*>(sc + kNaLev);
+    w.lvl_hist = reinterpret_cast<int*>(sc + kNaHist);
+    w.lvl_cursor = w.lvl_hist + kNaMax;
+    w.nlev = (int)(mbw * mbh);
     const KParams kp = make_kparams(p);
-    sk::build_queue_kernel<<<1, sk::kThreads, 0, stream>>>(w);
+    sk::queue_levels_kernel<<<1, sk::kThreads, 0, stream>>>(w, kp.concealed_is_support);
+    sk::queue_offsets_kernel<<<1, sk::kThreads, 0, stream>>>(w);
+    sk::queue_fill_kernel<<<1, sk::kThreads, 0, stream>>>(w);
     SK_CHECK(cudaGetLastError());
     long long grid = (long long)nd->sm_count * nd->blocks_per_sm;
     if (grid > mbw * mbh) grid = mbw * mbh;

@@ -108,11 +108,15 @@ struct WorkDev {
     const CUtensorMap* tmaps;
     int nframes;
     int* entry_of_mb;         // per block of all frames: queue entry or -1
-    int4* entries;            // (frame, block index, rank among the frame's lost blocks, 0)
+    int4* entries;            // (frame, block index, rank among the frame's lost blocks, level)
     int* counters;            // [0] entries, [1] queue head, [2] error word
     unsigned* done;           // per entry: 0 pending, 1 done, 2 done with error
     float* vals;              // per entry: 256 unrounded values of the block
     unsigned long long* stats;
+    int* level_of_mb;         // per block of all frames: dependency level (-1 received)
+    int* lvl_hist;            // per level: number of lost blocks, then the level's first entry
+    int* lvl_cursor;          // per level: entries handed out so far
+    int nlev;                 // levels allocated (>= blocks of the largest frame)
 };
 
 struct TraceRec {             // layout of skmmse_trace_rec
@@ -1459,34 +1463,134 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(WorkDev W, KParams
 }
 
 // ------------------------------------------------------------------------------------
-// queue construction: one CTA per frame; entries of a frame in raster order
+// Queue construction.  The queue lists every lost block of every frame ordered by its
+// dependency level: level 0 for a block none of whose earlier-in-raster lost neighbours
+// (left, top-left, top, top-right) is support, else 1 + the largest level among them.
+// Every dependency of an entry therefore sits at a lower level, earlier in the queue, so
+// a CTA only waits for blocks that running CTAs already hold (no deadlock), and blocks of
+// one level, independent of each other, run side by side.
 
-__global__ void __launch_bounds__(kThreads) build_queue_kernel(WorkDev W) {
+struct SegFV {
+    int f;  // a segment starts inside the combined range
+    int v;  // running maximum since the last segment start
+};
+
+__device__ __forceinline__ SegFV seg_combine(SegFV a, SegFV b) {
+    return {a.f | b.f, b.f ? b.v : max(a.v, b.v)};
+}
+
+// inclusive segmented max-scan over the CTA (one element per thread, thread order)
+__device__ __forceinline__ SegFV block_seg_scan(SegFV x, SegFV* sh /*[kWarps]*/) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        SegFV y;
+        y.f = __shfl_up_sync(0xffffffffu, x.f, o);
+        y.v = __shfl_up_sync(0xffffffffu, x.v, o);
+        if (lane >= o) x = seg_combine(y, x);
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid > 0) {
+        SegFV pre = sh[0];
+        for (int w = 1; w < wid; ++w) pre = seg_combine(pre, sh[w]);
+        x = seg_combine(pre, x);
+    }
+    __syncthreads();
+    return x;
+}
+
+constexpr int kLevelNeg = -(1 << 29);
+
+// one CTA per frame: dependency level of every lost block, row by row.  Within a row a run
+// of lost blocks chains through the left neighbour, so level[x] = x + max over the run up
+// to x of (up[k] - k), up[k] = max(0, 1 + level of the lost blocks above k): a segmented
+// max-scan.  Also counts the lost blocks of each level and of the whole call.
+__global__ void __launch_bounds__(kThreads) queue_levels_kernel(WorkDev W, int support) {
+    __shared__ SegFV sh[kWarps];
+    __shared__ int carry_s;
+    __shared__ int cnt_s;
+    const int f = blockIdx.x, tid = threadIdx.x;
+    const FrameDev& F = W.frames[f];
+    int* lev = W.level_of_mb + F.mb_base;
+    if (tid == 0) cnt_s = 0;
+    int cnt = 0;
+    for (int y = 0; y < F.mbh; ++y) {
+        if (tid == 0) carry_s = kLevelNeg;
+        __syncthreads();
+        for (int x0 = 0; x0 < F.mbw; x0 += kThreads) {
+            const int x = x0 + tid;
+            const bool lost = x < F.mbw && F.lost[y * F.mbw + x] != 0;
+            int up = 0;
+            if (lost && support && y > 0) {
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int xx = x + dx;
+                    if (xx >= 0 && xx < F.mbw && F.lost[(y - 1) * F.mbw + xx])
+                        up = max(up, lev[(y - 1) * F.mbw + xx] + 1);
+                }
+            }
+            const bool left_lost = x > 0 && x - 1 < F.mbw && F.lost[y * F.mbw + x - 1] != 0;
+            SegFV e;
+            e.f = (!lost || !left_lost || !support) ? 1 : 0;
+            e.v = lost ? up - x : kLevelNeg;
+            // a run continuing from the previous chunk starts without a head in this chunk
+            if (tid == 0 && x0 > 0 && lost && left_lost && support) e.f = 0;
+            SegFV r = block_seg_scan(e, sh);
+            const int carry = carry_s;
+            if (!r.f) r.v = max(r.v, carry);
+            int level = -1;
+            if (lost) {
+                level = support ? x + r.v : 0;
+                lev[y * F.mbw + x] = level;
+                atomicAdd(&W.lvl_hist[level], 1);
+                ++cnt;
+            } else if (x < F.mbw) {
+                lev[y * F.mbw + x] = -1;
+            }
+            __syncthreads();
+            if (tid == kThreads - 1) carry_s = (lost && support) ? r.v : kLevelNeg;
+            __syncthreads();
+        }
+    }
+    atomicAdd(&cnt_s, cnt);
+    __syncthreads();
+    if (tid == 0) atomicAdd(&W.counters[0], cnt_s);
+}
+
+// one CTA: exclusive scan of the level histogram into first-entry offsets
+__global__ void __launch_bounds__(kThreads) queue_offsets_kernel(WorkDev W) {
     __shared__ int scan[kWarps + 1];
-    __shared__ int base_s;
+    int run = 0;
+    for (int l0 = 0; l0 < W.nlev; l0 += kThreads) {
+        const int l = l0 + threadIdx.x;
+        const int v = l < W.nlev ? W.lvl_hist[l] : 0;
+        int tot;
+        const int ex = block_exscan(v, scan, &tot) + run;
+        if (l < W.nlev) W.lvl_hist[l] = ex;
+        run += tot;
+    }
+}
+
+// one CTA per frame: every lost block takes the next entry of its level; the rank among
+// the frame's lost blocks in raster order indexes its trace records
+__global__ void __launch_bounds__(kThreads) queue_fill_kernel(WorkDev W) {
+    __shared__ int scan[kWarps + 1];
     const int f = blockIdx.x;
     const FrameDev& F = W.frames[f];
     const int nmb = F.mbw * F.mbh;
-    // count
-    int cnt = 0;
-    for (int i = threadIdx.x; i < nmb; i += kThreads) cnt += F.lost[i] != 0;
-    int total;
-    (void)block_exscan(cnt, scan, &total);
-    if (threadIdx.x == 0) base_s = atomicAdd(&W.counters[0], total);
-    __syncthreads();
-    const int base = base_s;
-    // ranks in raster order: process in tiles of kThreads
     int run = 0;
     for (int t0 = 0; t0 < nmb; t0 += kThreads) {
         const int i = t0 + threadIdx.x;
         const int lost = (i < nmb) ? (F.lost[i] != 0) : 0;
         int tot;
-        const int r = block_exscan(lost, scan, &tot) + run;
+        const int rank = block_exscan(lost, scan, &tot) + run;
         if (i < nmb) {
             if (lost) {
-                W.entry_of_mb[F.mb_base + i] = base + r;
-                W.entries[base + r] = make_int4(f, i, r, 0);
-                W.done[base + r] = 0u;
+                const int level = W.level_of_mb[F.mb_base + i];
+                const int e = W.lvl_hist[level] + atomicAdd(&W.lvl_cursor[level], 1);
+                W.entry_of_mb[F.mb_base + i] = e;
+                W.entries[e] = make_int4(f, i, rank, level);
+                W.done[e] = 0u;
             } else {
                 W.entry_of_mb[F.mb_base + i] = -1;
             }

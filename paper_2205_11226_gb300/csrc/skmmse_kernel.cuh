@@ -134,19 +134,19 @@ struct TraceRec {             // layout of skmmse_trace_rec
 
 struct __align__(16) HqlP1 {                 // covariance / factorisation phase
     int cint[36][36];
-    float cfrac[36][37];
+    float cfrac[36][36];
     df32 A[32][33];
     df32 X[32][33];
 };
-struct __align__(16) HqlP2 {                 // distance / beta / alpha phase
-    __align__(16) float U[kCh][36];  // whitened chunk
-    float W[kMaxI0][kCh + 4];  // weights (beta pass: [beta][j]; alpha pass: [i][j])
-    float accB[kMaxBeta][kZs];
-    float accI[kMaxI0][kZs];
+struct __align__(16) HqlP2 {                 // beta / leave-one-out phase
+    union {
+        __align__(16) float Vs[kCh][kZs];    // whitened chunk: x'(4) u(32) 1 pad(3)
+        float mrg[kThreads][37];             // per-thread partial sums before a merge
+    };
+    float mI[kThreads];                      // per-thread running maxima (leave-one-out)
     __align__(16) float UI[kMaxI0][36];
     float XI[kMaxI0][4];
-    float mI[kMaxI0];
-    float scaleI[kMaxI0];
+    float accI[kMaxI0][37];                  // merged leave-one-out sums: x'(4) u(32) sum w
 };
 
 struct __align__(16) Hql {
@@ -171,7 +171,9 @@ struct __align__(16) Hql {
     int scan[kWarps + 1];
     int hist[256];
     int sel[4];
-    float colN[36], colF[36];
+    int colNi[36];
+    float colF[36];
+    int koff[kZs];
     float lam;
     float alpha;
     union {
@@ -466,45 +468,86 @@ __device__ __forceinline__ int idl_step(Smem& sm, const KParams& P, const StepCt
 // ------------------------------------------------------------------------------------
 // HQL
 
+// per-column source of a staged candidate row: S offset relative to the window top-left,
+// or -1 (zero padding), -2 (the constant-one column)
+__device__ __forceinline__ void hql_build_koff(Hql& h, int nz) {
+    const int tid = threadIdx.x;
+    if (tid < kZs) {
+        int o = -1;
+        if (tid < nz) o = (tid < 4) ? (tid >> 1) * kReg + (tid & 1) + 2 * kReg + 2 : h.off[tid - 4];
+        else if (tid == 36) o = -2;
+        h.koff[tid] = o;
+    }
+}
+
 // stage candidates [c0, c0+n) into Z[buf]: x' (4), y' (ny), 1, zero padding
-__device__ __forceinline__ bool hql_stage(Smem& sm, int buf, int c0, int n, int nz,
-                                          float shift) {
+__device__ __forceinline__ void hql_stage(Smem& sm, int buf, int c0, int n, float shift) {
     Hql& h = sm.hql;
-    bool frac = false;
+#pragma unroll 2
     for (int idx = threadIdx.x; idx < kCh * kZs; idx += kThreads) {
         const int j = idx / kZs, k = idx - j * kZs;
+        const int o = h.koff[k];
         float v = 0.0f;
         if (j < n) {
-            const int base = h.cand[c0 + j];
-            if (k < nz) {
-                int o;
-                if (k < 4) o = (k >> 1) * kReg + (k & 1) + 2 * kReg + 2;
-                else o = h.off[k - 4];
-                v = sm.S[base + o] - shift;
-                frac = frac || (v != rintf(v));
-            } else if (k == 36) {
-                v = 1.0f;
-            }
+            if (o >= 0) v = sm.S[h.cand[c0 + j] + o] - shift;
+            else if (o == -2) v = 1.0f;
         }
         h.Z[buf][j][k] = v;
+    }
+}
+
+// stage the integer parts (as int) into Z[0] and the fractions into Z[1]; returns whether
+// this thread saw a non-integer value
+__device__ __forceinline__ bool hql_stage_split(Smem& sm, int c0, int n, float shift) {
+    Hql& h = sm.hql;
+    bool frac = false;
+    int* zi = reinterpret_cast<int*>(&h.Z[0][0][0]);
+    float* zf = &h.Z[1][0][0];
+#pragma unroll 2
+    for (int idx = threadIdx.x; idx < kCh * kZs; idx += kThreads) {
+        const int j = idx / kZs, k = idx - j * kZs;
+        const int o = h.koff[k];
+        float v = 0.0f;
+        if (j < n && o >= 0) v = sm.S[h.cand[c0 + j] + o] - shift;
+        const float nv = rintf(v);
+        zi[idx] = __float2int_rn(nv);
+        zf[idx] = v - nv;
+        frac = frac || (v != nv);
     }
     return frac;
 }
 
-// enumerate the 44 covariance tiles (ta <= tb, not (0,0)) of the 9x9 grid of 4x4 tiles
-__device__ __forceinline__ void cov_tile(int t, int* ta, int* tb) {
-    int idx = t + 1;  // skip (0,0)
-    int a = 0;
-    while (idx >= 9 - a) {
-        idx -= 9 - a;
-        ++a;
+// whitened coordinates of candidates tj, tj+1 (rows of Z[buf]), coordinates 4tq..4tq+3:
+// u = L^-1 (y_j - y0)
+__device__ __forceinline__ void whiten_tile(const Hql& h, int buf, int ny, int tj, int tq,
+                                            float u0[4], float u1[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        u0[q] = 0.0f;
+        u1[q] = 0.0f;
     }
-    *ta = a;
-    *tb = a + idx;
+    for (int l4 = 0; l4 <= tq; ++l4) {
+        if (4 * l4 >= ny) break;
+        const float4 e0v = *reinterpret_cast<const float4*>(&h.Z[buf][tj][4 + 4 * l4]);
+        const float4 e1v = *reinterpret_cast<const float4*>(&h.Z[buf][tj + 1][4 + 4 * l4]);
+        const float4 ysv = *reinterpret_cast<const float4*>(&h.ys[4 * l4]);
+        const float e0[4] = {e0v.x - ysv.x, e0v.y - ysv.y, e0v.z - ysv.z, e0v.w - ysv.w};
+        const float e1[4] = {e1v.x - ysv.x, e1v.y - ysv.y, e1v.z - ysv.z, e1v.w - ysv.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 lv = *reinterpret_cast<const float4*>(&h.Linv[4 * tq + q][4 * l4]);
+            const float L4[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                u0[q] = __fmaf_rn(L4[r], e0[r], u0[q]);
+                u1[q] = __fmaf_rn(L4[r], e1[r], u1[q]);
+            }
+        }
+    }
 }
 
 __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepCtx& c, float xhat[4],
-                         TraceRec* tr, bool trace) {
+                                         TraceRec* tr, bool trace) {
     Hql& h = sm.hql;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ny = c.ny, nz = ny + 4;
@@ -536,113 +579,96 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
             }
         }
         int total;
-        int pos = block_exscan(cnt, h.scan, &total);
+        int pos = block_exscan(cnt, h.scan, &total);  // (barriers: the lists above are visible)
         for (int q = 0; q < 8; ++q)
             if ((flags >> q) & 1u) {
                 const int p = tid * 8 + q;
                 h.cand[pos++] = (uint16_t)((p / kNpos) * kReg + (p % kNpos));
             }
         if (tid == 0) h.M = total;
+        hql_build_koff(h, nz);
     }
     __syncthreads();
     const int M = h.M;
+    const int nchunks = (M + kCh - 1) / kCh;
     SK_PHASE(PH_H0);
 
-    // H1: mean and covariance of z' = z - shift, Eq. (8).  Integer parts accumulate
-    // exactly (|n'| <= 255, at most kCh products per thread per chunk < 2^24), the
-    // fractional cross terms separately; the chunk sums go to int32.
-    int ta = 0, tb = 0;
-    const bool tile_thread = tid < 220;
-    const int grp = tid / 44;
-    if (tile_thread) cov_tile(tid % 44, &ta, &tb);
-    const bool tile_active = tile_thread && (4 * tb < nz);
-    int ci[16];
-    float cf[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        ci[q] = 0;
-        cf[q] = 0.0f;
-    }
-    float colN = 0.0f, colF = 0.0f;
-    for (int idx = tid; idx < 36 * 36; idx += kThreads) {
-        h.p1.cint[idx / 36][idx % 36] = 0;
-    }
-    const int nchunks = (M + kCh - 1) / kCh;
+    // H1: sums of z' and z' z'^T, z' = z - shift (Eq. (8)).  Thread (a, g) owns row a of the
+    // product matrix over the candidates j = g (mod kG1).  Integer parts multiply and
+    // accumulate exactly in int32 (|n| <= 255, at most 1849 products: < 2^31); fractional
+    // cross terms accumulate in FP32 (they are small).
     {
-        bool frac = hql_stage(sm, 0, 0, min(kCh, M), nz, shift);
+        constexpr int kG1 = kThreads / 36;
+        const int a = tid % 36, g = tid / 36;
+        const bool act = g < kG1 && a < nz;
+        int ai[36];
+        float af[36];
+#pragma unroll
+        for (int b = 0; b < 36; ++b) {
+            ai[b] = 0;
+            af[b] = 0.0f;
+        }
+        int colN = 0;
+        float colF = 0.0f;
+        for (int idx = tid; idx < 36 * 36; idx += kThreads) {
+            h.p1.cint[idx / 36][idx % 36] = 0;
+            h.p1.cfrac[idx / 36][idx % 36] = 0.0f;
+            if (idx < 36) h.colNi[idx] = 0;
+        }
+        const int* zi = reinterpret_cast<const int*>(&h.Z[0][0][0]);
+        const float* zf = &h.Z[1][0][0];
         for (int ch = 0; ch < nchunks; ++ch) {
-            const int buf = ch & 1, c0 = ch * kCh, n = min(kCh, M - c0);
+            const int c0 = ch * kCh, n = min(kCh, M - c0);
+            if (ch > 0) __syncthreads();  // previous chunk consumed
+            const bool frac = hql_stage_split(sm, c0, n, shift);
             const bool any_frac = __syncthreads_or(frac) != 0;
-            if (tile_active) {
-                float ai[16];
+            if (act) {
+                for (int j = g; j < n; j += kG1) {
+                    const int na = zi[j * kZs + a];
+                    const float fa = zf[j * kZs + a];
+                    colN += na;
+                    colF += fa;
 #pragma unroll
-                for (int q = 0; q < 16; ++q) ai[q] = 0.0f;
-                for (int j = grp; j < n; j += 5) {
-                    const float4 za = *reinterpret_cast<const float4*>(&h.Z[buf][j][4 * ta]);
-                    const float4 zb = *reinterpret_cast<const float4*>(&h.Z[buf][j][4 * tb]);
-                    const float a[4] = {za.x, za.y, za.z, za.w};
-                    const float b[4] = {zb.x, zb.y, zb.z, zb.w};
-                    float na[4], nb[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        na[q] = rintf(a[q]);
-                        nb[q] = rintf(b[q]);
+                    for (int b4 = 0; b4 < 9; ++b4) {
+                        const int4 nb = *reinterpret_cast<const int4*>(&zi[j * kZs + 4 * b4]);
+                        ai[4 * b4 + 0] += na * nb.x;
+                        ai[4 * b4 + 1] += na * nb.y;
+                        ai[4 * b4 + 2] += na * nb.z;
+                        ai[4 * b4 + 3] += na * nb.w;
                     }
-#pragma unroll
-                    for (int p = 0; p < 4; ++p)
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) ai[p * 4 + q] = __fmaf_rn(na[p], nb[q], ai[p * 4 + q]);
                     if (any_frac) {
+                        const float naf = (float)na;
 #pragma unroll
-                        for (int p = 0; p < 4; ++p)
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const float fb = b[q] - nb[q], fa = a[p] - na[p];
-                                cf[p * 4 + q] = __fmaf_rn(na[p], fb, cf[p * 4 + q]);
-                                cf[p * 4 + q] = __fmaf_rn(fa, b[q], cf[p * 4 + q]);
-                            }
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 16; ++q) ci[q] += __float2int_rn(ai[q]);
-            } else if (tid >= 220) {
-                const int k = tid - 220;
-                if (k < nz) {
-                    for (int j = 0; j < n; ++j) {
-                        const float v = h.Z[buf][j][k];
-                        const float nv = rintf(v);
-                        colN += nv;
-                        colF += v - nv;
+                        for (int b4 = 0; b4 < 9; ++b4) {
+                            const int4 nb = *reinterpret_cast<const int4*>(&zi[j * kZs + 4 * b4]);
+                            const float4 fb = *reinterpret_cast<const float4*>(&zf[j * kZs + 4 * b4]);
+                            // n_a f_b + f_a (n_b + f_b)
+                            af[4 * b4 + 0] = __fmaf_rn(naf, fb.x, __fmaf_rn(fa, (float)nb.x + fb.x, af[4 * b4 + 0]));
+                            af[4 * b4 + 1] = __fmaf_rn(naf, fb.y, __fmaf_rn(fa, (float)nb.y + fb.y, af[4 * b4 + 1]));
+                            af[4 * b4 + 2] = __fmaf_rn(naf, fb.z, __fmaf_rn(fa, (float)nb.z + fb.z, af[4 * b4 + 2]));
+                            af[4 * b4 + 3] = __fmaf_rn(naf, fb.w, __fmaf_rn(fa, (float)nb.w + fb.w, af[4 * b4 + 3]));
+                        }
                     }
                 }
             }
-            if (ch + 1 < nchunks) frac = hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), nz, shift);
-        }
-    }
-    __syncthreads();
-    if (tile_active) {
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) atomicAdd(&h.p1.cint[4 * ta + p][4 * tb + q], ci[p * 4 + q]);
-    }
-    for (int g = 0; g < 5; ++g) {
-        if (tile_active && grp == g) {
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float& dst = h.p1.cfrac[4 * ta + p][4 * tb + q];
-                    dst = (g == 0) ? cf[p * 4 + q] : dst + cf[p * 4 + q];
-                }
         }
         __syncthreads();
+        if (act) {
+#pragma unroll
+            for (int b = 0; b < 36; ++b)
+                if (ai[b]) atomicAdd(&h.p1.cint[a][b], ai[b]);
+            atomicAdd(&h.colNi[a], colN);
+        }
+        // fractional sums in a fixed order of the subsets (deterministic)
+        for (int gg = 0; gg < kG1; ++gg) {
+            if (act && g == gg) {
+#pragma unroll
+                for (int b = 0; b < 36; ++b) h.p1.cfrac[a][b] += af[b];
+                h.colF[a] = (gg == 0) ? colF : h.colF[a] + colF;
+            }
+            __syncthreads();
+        }
     }
-    if (tid >= 220 && tid - 220 < 36) {
-        h.colN[tid - 220] = colN;
-        h.colF[tid - 220] = colF;
-    }
-    __syncthreads();
     SK_PHASE(PH_H1);
 
     // finalise C_ab = S_ab/M - T_a T_b / M^2 in double-float; YY (+ridge later), XY
@@ -652,8 +678,8 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
             const int a = idx / 36, b = idx % 36;
             if (a > b || b < 4 || b >= nz) continue;
             const df32 S = df_add(df_from_int(h.p1.cint[a][b]), df_make(h.p1.cfrac[a][b]));
-            const df32 Ta = df_two_sum(h.colN[a], h.colF[a]);
-            const df32 Tb = df_two_sum(h.colN[b], h.colF[b]);
+            const df32 Ta = df_add(df_from_int(h.colNi[a]), df_make(h.colF[a]));
+            const df32 Tb = df_add(df_from_int(h.colNi[b]), df_make(h.colF[b]));
             const df32 Cab = df_sub(df_mul(S, invM), df_mul(df_mul(Ta, invM), df_mul(Tb, invM)));
             if (a >= 4) {
                 h.p1.A[b - 4][a - 4] = Cab;  // lower triangle (row >= col)
@@ -683,21 +709,23 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
     // Cholesky / inverse factor in double-float: Gaussian elimination A = Lu D Lu^T and
     // the same row operations applied to I give X = Lu^-1; then L^-1 = D^-1/2 X.
     {
-        int pi[3], pj[3];
+        constexpr int kPairs = 528;  // lower-triangle entries of a 32 x 32 matrix
+        constexpr int kPer = (kPairs + kThreads - 1) / kThreads;
+        int pi[kPer], pj[kPer];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
+        for (int q = 0; q < kPer; ++q) {
             const int p = tid + q * kThreads;
             int i = (int)((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);
             while ((i + 1) * (i + 2) / 2 <= p) ++i;
             while (i * (i + 1) / 2 > p) --i;
-            pi[q] = (p < 528) ? i : 99;
+            pi[q] = (p < kPairs) ? i : 99;
             pj[q] = p - i * (i + 1) / 2;
         }
         for (int k = 0; k < ny; ++k) {
             const df32 akk = h.p1.A[k][k];
             const df32 rinv = df_div(df_make(1.0f), akk);
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
+            for (int q = 0; q < kPer; ++q) {
                 const int i = pi[q], j = pj[q];
                 if (i >= ny || i <= k) continue;
                 const df32 mlt = df_mul(h.p1.A[i][k], rinv);
@@ -745,45 +773,19 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
             for (int i = j; i < ny; ++i) kk = df_add(kk, df_mul(h.p1.A[a][i], h.p1.X[i][j]));
         h.K[a][j] = kk;
     }
-
     SK_PHASE(PH_CHOL);
+
     // H2: whitened distances d_j = ||L^-1 (y_j - y0)||^2 (Mahalanobis, Eq. (6) with C_YY)
     // thread tile: 2 candidates x 4 whitened coordinates
     const int tj = (tid >> 3) * 2, tq = tid & 7;
-    auto whiten_tile = [&](int buf, float u0[4], float u1[4]) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            u0[q] = 0.0f;
-            u1[q] = 0.0f;
-        }
-        for (int l4 = 0; l4 <= tq; ++l4) {
-            if (4 * l4 >= ny) break;
-            const float4 e0v = *reinterpret_cast<const float4*>(&h.Z[buf][tj][4 + 4 * l4]);
-            const float4 e1v = *reinterpret_cast<const float4*>(&h.Z[buf][tj + 1][4 + 4 * l4]);
-            const float4 ysv = *reinterpret_cast<const float4*>(&h.ys[4 * l4]);
-            const float e0[4] = {e0v.x - ysv.x, e0v.y - ysv.y, e0v.z - ysv.z, e0v.w - ysv.w};
-            const float e1[4] = {e1v.x - ysv.x, e1v.y - ysv.y, e1v.z - ysv.z, e1v.w - ysv.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 lv = *reinterpret_cast<const float4*>(&h.Linv[4 * tq + q][4 * l4]);
-                const float L4[4] = {lv.x, lv.y, lv.z, lv.w};
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    u0[q] = __fmaf_rn(L4[r], e0[r], u0[q]);
-                    u1[q] = __fmaf_rn(L4[r], e1[r], u1[q]);
-                }
-            }
-        }
-    };
     float lmin = INFINITY;
     {
-        bool dummy = hql_stage(sm, 0, 0, min(kCh, M), nz, shift);
-        (void)dummy;
+        hql_stage(sm, 0, 0, min(kCh, M), shift);
         for (int ch = 0; ch < nchunks; ++ch) {
             const int buf = ch & 1, c0 = ch * kCh, n = min(kCh, M - c0);
             __syncthreads();
             float u0[4], u1[4];
-            whiten_tile(buf, u0, u1);
+            whiten_tile(h, buf, ny, tj, tq, u0, u1);
             float p0 = 0.0f, p1 = 0.0f;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -805,10 +807,7 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
                     lmin = fminf(lmin, p1);
                 }
             }
-            if (ch + 1 < nchunks) {
-                bool d2 = hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), nz, shift);
-                (void)d2;
-            }
+            if (ch + 1 < nchunks) hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), shift);
         }
     }
     lmin = warp_max(-lmin);
@@ -823,79 +822,58 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
     const float dmin = h.dmin;
     SK_PHASE(PH_H2);
 
-    // H3: beta grid, Eqs. (9)-(10): accB[b][k] = sum_j w_j(b) z'_j[k], column 36 = sum w
+    // H3: beta grid, Eqs. (9)-(10).  Thread (b, g) owns beta_b over the candidates
+    // j = g (mod kG3): acc[k] = sum_j w_j(b) z'_j[k] for the staged columns (x', y', 1).
+    // Subset partial sums merge in double-float.
     const int nb = P.nbeta;
-    // tiles: one beta x 4 columns; thread owns tiles tid and tid + 256 (nb <= 32)
-    // per-chunk FP32 partial sums are added into double-float accumulators, so the
-    // rounding error does not grow with the number of candidates
-    const int bt0 = tid / 10, kq0 = tid % 10, bt1 = (tid + kThreads) / 10, kq1 = (tid + kThreads) % 10;
-    df32 ab0[4], ab1[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        ab0[q] = df_make(0.0f);
-        ab1[q] = df_make(0.0f);
-    }
-    auto beta_weights = [&](int buf, int c0, int n) {
-        for (int idx = tid; idx < kMaxBeta * kCh; idx += kThreads) {
-            const int b = idx / kCh, j = idx % kCh;
-            float w = 0.0f;
-            if (b < nb && j < n) w = expf(-(h.d[c0 + j] - dmin) * P.inv2beta[b]);
-            h.p2.W[b][j] = w;  // rows 0..31 of W (kMaxBeta <= kMaxI0)
-        }
-        (void)buf;
-    };
     {
-        bool dd = hql_stage(sm, 0, 0, min(kCh, M), nz, shift);
-        (void)dd;
+        const int G3 = kThreads / nb;
+        const int b = tid % nb, g = tid / nb;
+        const bool act = g < G3;
+        const float ib = P.inv2beta[b];
+        float acc[kZs];
+#pragma unroll
+        for (int k = 0; k < kZs; ++k) acc[k] = 0.0f;
+        hql_stage(sm, 0, 0, min(kCh, M), shift);
         for (int ch = 0; ch < nchunks; ++ch) {
             const int buf = ch & 1, c0 = ch * kCh, n = min(kCh, M - c0);
-            __syncthreads();  // previous chunk's accumulation done, stage(buf) done
-            beta_weights(buf, c0, n);
             __syncthreads();
-            auto beta_acc = [&](int bt, int kq, df32* abd) {
-                if (bt >= nb) return;
-                float ab[4] = {0.f, 0.f, 0.f, 0.f};
-                for (int j = 0; j < n; ++j) {
-                    const float w = h.p2.W[bt][j];
-                    const float4 z = *reinterpret_cast<const float4*>(&h.Z[buf][j][4 * kq]);
-                    ab[0] = __fmaf_rn(w, z.x, ab[0]);
-                    ab[1] = __fmaf_rn(w, z.y, ab[1]);
-                    ab[2] = __fmaf_rn(w, z.z, ab[2]);
-                    ab[3] = __fmaf_rn(w, z.w, ab[3]);
+            if (act) {
+                for (int j = g; j < n; j += G3) {
+                    const float w = expf(-(h.d[c0 + j] - dmin) * ib);
+#pragma unroll
+                    for (int k4 = 0; k4 < kZs / 4; ++k4) {
+                        const float4 z = *reinterpret_cast<const float4*>(&h.Z[buf][j][4 * k4]);
+                        acc[4 * k4 + 0] = __fmaf_rn(w, z.x, acc[4 * k4 + 0]);
+                        acc[4 * k4 + 1] = __fmaf_rn(w, z.y, acc[4 * k4 + 1]);
+                        acc[4 * k4 + 2] = __fmaf_rn(w, z.z, acc[4 * k4 + 2]);
+                        acc[4 * k4 + 3] = __fmaf_rn(w, z.w, acc[4 * k4 + 3]);
+                    }
                 }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) abd[q] = df_add(abd[q], df_make(ab[q]));
-            };
-            beta_acc(bt0, kq0, ab0);
-            beta_acc(bt1, kq1, ab1);
-            if (ch + 1 < nchunks) {
-                bool d2 = hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), nz, shift);
-                (void)d2;
             }
+            if (ch + 1 < nchunks) hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), shift);
         }
-    }
-    if (bt0 < nb) {
+        __syncthreads();
+        if (act) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            h.p2.accB[bt0][4 * kq0 + q] = df_to_f(ab0[q]);
-            h.accBd[bt0][4 * kq0 + q] = ab0[q];
+            for (int k = 0; k < 37; ++k) h.p2.mrg[tid][k] = acc[k];
         }
-    }
-    if (bt1 < nb) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            h.p2.accB[bt1][4 * kq1 + q] = df_to_f(ab1[q]);
-            h.accBd[bt1][4 * kq1 + q] = ab1[q];
+        __syncthreads();
+        for (int idx = tid; idx < nb * 37; idx += kThreads) {
+            const int bb = idx / 37, k = idx % 37;
+            df32 s = df_make(0.0f);
+            for (int gg = 0; gg < G3; ++gg) s = df_add(s, df_make(h.p2.mrg[gg * nb + bb][k]));
+            h.accBd[bb][k] = s;
         }
     }
     __syncthreads();
     // eps_y(b) = || y0 - y~0(b) ||^2 ; warp w handles b = w, w+8, ...
     for (int b = wid; b < nb; b += kWarps) {
-        const float inv = 1.0f / h.p2.accB[b][36];
         float e = 0.0f;
         if (lane < ny) {
-            const float r = h.p2.accB[b][4 + lane] * inv - h.ys[lane];
-            e = r * r;
+            const df32 r = df_sub(df_div(h.accBd[b][4 + lane], h.accBd[b][36]), df_make(h.ys[lane]));
+            const float rf = df_to_f(r);
+            e = rf * rf;
         }
         e = warp_sum(e);
         if (lane == 0) h.eps[b] = e;
@@ -935,8 +913,8 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
             if (lane == 0) h.corr[a] = df_neg(t);
         }
     }
-
     SK_PHASE(PH_H3);
+
     // H4: I0 = the n0 smallest d_j, ties to the lower index (radix select on the bits)
     int n0 = min(ny + 1, M - 1);
     if (n0 < 0) n0 = 0;
@@ -951,14 +929,35 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
                 if ((key & maskbits) == prefix) atomicAdd(&h.hist[(key >> shiftb) & 255u], 1);
             }
             __syncthreads();
-            if (tid == 0) {
-                int acc = 0, dg = 0;
-                for (dg = 0; dg < 256; ++dg) {
-                    if (acc + h.hist[dg] >= need) break;
-                    acc += h.hist[dg];
+            if (wid == 0) {
+                // first digit whose cumulative count reaches `need` (warp scan of 8 bins/lane)
+                int loc[8], s8 = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    loc[q] = h.hist[lane * 8 + q];
+                    s8 += loc[q];
                 }
-                h.sel[0] = dg;
-                h.sel[1] = need - acc;
+                int incl = s8;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int excl = incl - s8;
+                const unsigned hit = __ballot_sync(0xffffffffu, incl >= need);
+                const int src = __ffs(hit) - 1;
+                if (lane == src) {
+                    int acc = excl, dg = lane * 8;
+                    for (int q = 0; q < 8; ++q) {
+                        if (acc + loc[q] >= need) {
+                            dg = lane * 8 + q;
+                            break;
+                        }
+                        acc += loc[q];
+                    }
+                    h.sel[0] = dg;
+                    h.sel[1] = need - acc;
+                }
             }
             __syncthreads();
             prefix |= (unsigned)h.sel[0] << shiftb;
@@ -967,7 +966,6 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
             __syncthreads();
         }
         // members: key < prefix, plus the first `need` with key == prefix (index order)
-        int cnt = 0;
         unsigned f = 0, eqf = 0;
         const int per = (M + kThreads - 1) / kThreads;  // <= 8
         for (int q = 0; q < per; ++q) {
@@ -986,8 +984,7 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
                 if (eqpos < need) take |= 1u << q;
                 ++eqpos;
             }
-        cnt = __popc(take);
-        int pos = block_exscan(cnt, h.scan, &tot);
+        int pos = block_exscan(__popc(take), h.scan, &tot);
         for (int q = 0; q < per; ++q)
             if ((take >> q) & 1u) h.i0[pos++] = tid * per + q;
         __syncthreads();
@@ -1007,124 +1004,116 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
                 h.p2.XI[i][a] = sm.S[base + (a >> 1) * kReg + (a & 1) + 2 * kReg + 2] - shift;
             }
         }
-        if (tid < kMaxI0) {
-            h.p2.mI[tid] = kNegBig;
-        }
     }
     __syncthreads();
-
     SK_PHASE(PH_H4);
-    // H5: leave-one-out predictions for i in I0 at beta* (Eqs. (11)-(12))
+
+    // H5: leave-one-out predictions for i in I0 at beta* (Eqs. (11)-(12)).  Thread (i, g)
+    // owns member i over the candidates j = g (mod kG5): online max-subtracted softmax of
+    // -||u_i - u_j||^2 / (2 beta*) (j != i) and the weighted sums of [x'_j | u_j | 1].
     float num = 0.0f, den = 0.0f;
     if (n0 > 0) {
+        constexpr int kG5 = kThreads / kMaxI0;
         const float ib = P.inv2beta[bstar];
-        // accumulators: thread owns tiles (i, column quad) over accI[n0][40]
-        // tiles: one I0 member x 4 columns of [1 | x' | u]; thread owns tiles tid, tid+256
-        float acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
-        const int ti0 = tid / 10, tk0 = tid % 10;
-        const int ti1 = (tid + kThreads) / 10, tk1 = (tid + kThreads) % 10;
-        bool dd = hql_stage(sm, 0, 0, min(kCh, M), nz, shift);
-        (void)dd;
+        const int mi = tid % kMaxI0, g = tid / kMaxI0;
+        const bool act = g < kG5 && mi < n0;
+        const int self = act ? h.i0[mi] : -1;
+        float ui[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) ui[k] = act ? h.p2.UI[mi][k] : 0.0f;
+        float acc[37];
+#pragma unroll
+        for (int k = 0; k < 37; ++k) acc[k] = 0.0f;
+        float m = -INFINITY;
+        hql_stage(sm, 0, 0, min(kCh, M), shift);
         for (int ch = 0; ch < nchunks; ++ch) {
             const int buf = ch & 1, c0 = ch * kCh, n = min(kCh, M - c0);
-            __syncthreads();
-            // whitened chunk into U
+            __syncthreads();  // staged chunk visible; previous chunk's Vs consumed
             {
                 float u0[4], u1[4];
-                whiten_tile(buf, u0, u1);
+                whiten_tile(h, buf, ny, tj, tq, u0, u1);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    h.p2.U[tj][4 * tq + q] = u0[q];
-                    h.p2.U[tj + 1][4 * tq + q] = u1[q];
+                    h.p2.Vs[tj][4 + 4 * tq + q] = u0[q];
+                    h.p2.Vs[tj + 1][4 + 4 * tq + q] = u1[q];
                 }
-            }
-            __syncthreads();
-            // distances to the I0 members -> exponents in W
-            for (int idx = tid; idx < kMaxI0 * kCh; idx += kThreads) {
-                const int i = idx / kCh, j = idx % kCh;
-                float s = kNegBig;
-                if (i < n0 && j < n && (c0 + j) != h.i0[i]) {
-                    float dd2 = 0.0f;
-                    for (int k4 = 0; k4 < 8; ++k4) {
-                        if (4 * k4 >= ny) break;
-                        const float4 a = *reinterpret_cast<const float4*>(&h.p2.UI[i][4 * k4]);
-                        const float4 b = *reinterpret_cast<const float4*>(&h.p2.U[j][4 * k4]);
-                        float t;
-                        t = a.x - b.x; dd2 = __fmaf_rn(t, t, dd2);
-                        t = a.y - b.y; dd2 = __fmaf_rn(t, t, dd2);
-                        t = a.z - b.z; dd2 = __fmaf_rn(t, t, dd2);
-                        t = a.w - b.w; dd2 = __fmaf_rn(t, t, dd2);
-                    }
-                    s = -dd2 * ib;
-                }
-                h.p2.W[i][j] = s;
-            }
-            __syncthreads();
-            // online max per row, rescale factor, weights
-            for (int i = wid; i < n0; i += kWarps) {
-                const float s0v = h.p2.W[i][lane], s1v = h.p2.W[i][lane + 32];
-                const float cm = warp_max(fmaxf(s0v, s1v));
-                const float old = h.p2.mI[i];
-                const float nm = fmaxf(old, cm);
-                __syncwarp();
-                h.p2.W[i][lane] = (s0v <= kNegBig) ? 0.0f : expf(s0v - nm);
-                h.p2.W[i][lane + 32] = (s1v <= kNegBig) ? 0.0f : expf(s1v - nm);
-                if (lane == 0) {
-                    h.p2.scaleI[i] = expf(old - nm);
-                    h.p2.mI[i] = nm;
-                }
-            }
-            __syncthreads();
-            // acc[i][col] += sum_j W[i][j] * V[j][col], V = [1 | x' | u]
-            auto accum = [&](int ti, int tk, float* acc) {
-                if (ti >= n0) return;
-                const float sc = h.p2.scaleI[ti];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q] *= sc;
-                for (int j = 0; j < n; ++j) {
-                    const float w = h.p2.W[ti][j];
-                    float v[4];
+                if (tq == 0) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int col = 4 * tk + q;
-                        float x;
-                        if (col == 0) x = 1.0f;
-                        else if (col < 5) x = h.Z[buf][j][col - 1];
-                        else if (col < 37) x = h.p2.U[j][col - 5];
-                        else x = 0.0f;
-                        v[q] = x;
+                        h.p2.Vs[tj][q] = h.Z[buf][tj][q];
+                        h.p2.Vs[tj + 1][q] = h.Z[buf][tj + 1][q];
                     }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[q] = __fmaf_rn(w, v[q], acc[q]);
+                    h.p2.Vs[tj][36] = h.Z[buf][tj][36];
+                    h.p2.Vs[tj + 1][36] = h.Z[buf][tj + 1][36];
                 }
-            };
-            accum(ti0, tk0, acc0);
-            accum(ti1, tk1, acc1);
-            if (ch + 1 < nchunks) {
-                bool d2 = hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), nz, shift);
-                (void)d2;
+            }
+            __syncthreads();
+            if (ch + 1 < nchunks) hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), shift);
+            if (act) {
+                for (int j = g; j < n; j += kG5) {
+                    const float* v = &h.p2.Vs[j][0];
+                    float d = 0.0f;
+#pragma unroll
+                    for (int k4 = 0; k4 < 8; ++k4) {
+                        const float4 q = *reinterpret_cast<const float4*>(&v[4 + 4 * k4]);
+                        float t;
+                        t = ui[4 * k4 + 0] - q.x; d = __fmaf_rn(t, t, d);
+                        t = ui[4 * k4 + 1] - q.y; d = __fmaf_rn(t, t, d);
+                        t = ui[4 * k4 + 2] - q.z; d = __fmaf_rn(t, t, d);
+                        t = ui[4 * k4 + 3] - q.w; d = __fmaf_rn(t, t, d);
+                    }
+                    if (c0 + j == self) continue;
+                    const float s = -d * ib;
+                    if (s > m) {
+                        const float sc = expf(m - s);
+#pragma unroll
+                        for (int k = 0; k < 37; ++k) acc[k] *= sc;
+                        m = s;
+                    }
+                    const float w = expf(s - m);
+#pragma unroll
+                    for (int k4 = 0; k4 < 9; ++k4) {
+                        const float4 q = *reinterpret_cast<const float4*>(&v[4 * k4]);
+                        acc[4 * k4 + 0] = __fmaf_rn(w, q.x, acc[4 * k4 + 0]);
+                        acc[4 * k4 + 1] = __fmaf_rn(w, q.y, acc[4 * k4 + 1]);
+                        acc[4 * k4 + 2] = __fmaf_rn(w, q.z, acc[4 * k4 + 2]);
+                        acc[4 * k4 + 3] = __fmaf_rn(w, q.w, acc[4 * k4 + 3]);
+                    }
+                    acc[36] += w;
+                }
             }
         }
-        if (ti0 < n0) {
+        __syncthreads();  // Vs no longer needed: its storage takes the partial sums
+        if (act) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) h.p2.accI[ti0][4 * tk0 + q] = acc0[q];
+            for (int k = 0; k < 37; ++k) h.p2.mrg[tid][k] = acc[k];
+            h.p2.mI[tid] = m;
         }
-        if (ti1 < n0) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) h.p2.accI[ti1][4 * tk1 + q] = acc1[q];
+        __syncthreads();
+        // merge the subsets of each member with the max-subtracted rescaling
+        for (int idx = tid; idx < n0 * 37; idx += kThreads) {
+            const int i = idx / 37, k = idx % 37;
+            float mm = -INFINITY;
+            for (int gg = 0; gg < kG5; ++gg) mm = fmaxf(mm, h.p2.mI[gg * kMaxI0 + i]);
+            float sacc = 0.0f;
+            for (int gg = 0; gg < kG5; ++gg) {
+                const float mg = h.p2.mI[gg * kMaxI0 + i];
+                if (mg > -INFINITY) sacc += h.p2.mrg[gg * kMaxI0 + i][k] * expf(mg - mm);
+            }
+            h.p2.accI[i][k] = sacc;
         }
         __syncthreads();
         // r_i = x_i - x~_i ; g_i = G (u_i - u~_i) ; alpha = sum r.g / sum g.g
         if (tid < 4 * kMaxI0) {
             const int i = tid >> 2, a = tid & 3;
             if (i < n0) {
-                const float inv = 1.0f / h.p2.accI[i][0];
-                const float r = h.p2.XI[i][a] - h.p2.accI[i][1 + a] * inv;
-                float g = 0.0f;
+                const float inv = 1.0f / h.p2.accI[i][36];
+                const float r = h.p2.XI[i][a] - h.p2.accI[i][a] * inv;
+                float gg = 0.0f;
                 for (int k = 0; k < ny; ++k)
-                    g = __fmaf_rn(h.G[a][k], h.p2.UI[i][k] - h.p2.accI[i][5 + k] * inv, g);
-                num = r * g;
-                den = g * g;
+                    gg = __fmaf_rn(h.G[a][k], h.p2.UI[i][k] - h.p2.accI[i][4 + k] * inv, gg);
+                num = r * gg;
+                den = gg * gg;
             }
         }
     }

@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--profile", default="efficient")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="batch",
+                    help="batch (the benchmark), or a smaller case for profiling")
     return ap.parse_args()
 
 
@@ -112,9 +114,21 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def build_workload(seed: int):
+WORKLOADS = {
+    "batch": WORKLOAD,
+    "slice1080p": "1920x1080_runs4-20_20pct_fine_texture",
+    "checkerboard": "512x512_checkerboard_25pct",
+    "single": "256x256_one_block",
+}
+
+
+def build_workload(seed: int, name: str = "batch"):
     from paper_2205_11226_gb300 import synth
-    return synth.workload_batch(seed)
+    if name == "batch":
+        return synth.workload_batch(seed)
+    f, m = {"slice1080p": synth.workload_slice_1080p, "checkerboard": synth.workload_checkerboard,
+            "single": synth.workload_single}[name](seed)
+    return [f], [m]
 
 
 def cpu_baseline(frames, masks, profile: str, budget_s: float = 25.0):
@@ -193,7 +207,7 @@ def run_ours(args):
         dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
     skbuild.build()
     from paper_2205_11226_gb300 import skmmse
-    frames, masks = build_workload(args.seed + 1000 * rank)
+    frames, masks = build_workload(args.seed + 1000 * rank, args.workload)
     p = skmmse.params(args.profile)
     ctx = skmmse.Context()
     stream = torch.cuda.current_stream()
@@ -290,7 +304,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded generator standing in for Kodak/ClassB/ClassC; no dataset)",
-            "config": {"workload": WORKLOAD, "frames": len(frames), "lost_mbs_per_step": n_lost,
+            "config": {"workload": WORKLOADS[args.workload], "frames": len(frames), "lost_mbs_per_step": n_lost,
                        "profile": args.profile, "precision": "fp32",
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replicas" if ws > 1 else "single"},
@@ -301,7 +315,7 @@ def run_ours(args):
             "layers": {k: st[k] for k in ("n_patches", "n_brl", "n_idl", "n_hql", "n_brl_nocand")},
             "wall_s_timed": t_wall,
             "clocks": clocks}
-    if ws == 1 and not args.no_cpu_baseline:
+    if ws == 1 and not args.no_cpu_baseline and args.workload == "batch":
         line["cpu_baseline"] = cpu_baseline(frames, masks, args.profile)
     print(json.dumps(line), flush=True)
     ctx.close()

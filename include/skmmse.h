@@ -190,6 +190,31 @@ skmmse_status skmmse_conceal_batch(skmmse_context* ctx, const skmmse_frame* h_fr
    Returns SKMMSE_ERR_TIMEOUT if a dependency wait gave up during that call. */
 skmmse_status skmmse_read_stats(skmmse_context* ctx, skmmse_stats* h_stats, void* stream);
 
+/* A batch call recorded as a CUDA graph on fixed frame buffers: the received-pixel copies,
+   the queue construction and the persistent concealment kernel.  The frame descriptors and
+   TMA maps are uploaded once, synchronously, into device memory owned by the graph (which
+   also owns its scratch); each launch conceals what the frame buffers hold when it runs,
+   asynchronously on `stream`.  Launches of one graph must be ordered on one stream. */
+typedef struct skmmse_graph skmmse_graph;
+skmmse_status skmmse_graph_create(skmmse_context* ctx, const skmmse_frame* h_frames, int n,
+                                  const skmmse_params* p, skmmse_graph** out);
+skmmse_status skmmse_graph_launch(skmmse_graph* g, void* stream);
+/* Synchronise `stream` and return the counters of the graph's last launch. */
+skmmse_status skmmse_graph_read_stats(skmmse_graph* g, skmmse_stats* h_stats, void* stream);
+void skmmse_graph_destroy(skmmse_graph* g);
+
+/* Autotuner of the persistent launch: conceals the given batch `reps` times (plus one
+   warm-up) for every number of CTAs per SM the kernel's occupancy allows (fewer CTAs give
+   each block more of the SM and shorten dependency chains; more CTAs run more blocks at
+   once), records the mean device time of each option in h_ms_per_option[k-1] (nullable,
+   8 entries) and keeps the fastest in the context (returned in *h_best, nullable).  The
+   outputs of the batch are written by every run.  Synchronous. */
+skmmse_status skmmse_autotune(skmmse_context* ctx, const skmmse_frame* h_frames, int n,
+                              const skmmse_params* p, int reps, void* stream,
+                              float* h_ms_per_option, int* h_best);
+/* Set the persistent CTAs per SM directly (0 = occupancy maximum). */
+skmmse_status skmmse_set_ctas_per_sm(skmmse_context* ctx, int ctas_per_sm);
+
 /* Largest frame, in 16x16 blocks (partial edge blocks included), that
    skmmse_conceal_noalloc accepts: 8192 covers 1920x1080 (120 x 68 = 8160 blocks). */
 #define SKMMSE_NOALLOC_MAX_MBS 8192

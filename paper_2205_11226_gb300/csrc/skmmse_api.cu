@@ -38,6 +38,7 @@ struct skmmse_context {
     cudaEvent_t stage_done = nullptr;
     bool stage_pending = false;
     long long last_nbeta = 0;
+    int ctas_per_sm = 0;  // persistent CTAs per SM (0: occupancy maximum; set by the autotuner)
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
 };
 
@@ -105,6 +106,136 @@ KParams make_kparams(const skmmse_params* p) {
     k.concealed_is_support = p->concealed_is_support ? 1 : 0;
     k.flags = p->flags;
     return k;
+}
+
+
+// ------------------------------------------------------------------------------------
+// batch planning shared by direct calls and graph capture
+
+struct BatchLayout {
+    long long total_mbs = 0, max_mbs = 1;
+    size_t o_frames = 0, o_tmaps = 0, o_eom = 0, o_ent = 0, o_done = 0, o_vals = 0, o_lev = 0,
+           o_hist = 0, need = 0, stage_bytes = 0;
+};
+
+skmmse_status plan_batch(const skmmse_frame* frames, int n, const skmmse_params* p, BatchLayout* L) {
+    if (n > 65536) return SKMMSE_ERR_SHAPE;
+    skmmse_status s = validate_params(p);
+    if (s != SKMMSE_OK) return s;
+    for (int i = 0; i < n; ++i) {
+        s = validate_frame(frames[i]);
+        if (s != SKMMSE_OK) return s;
+        const long long mbw = (frames[i].width + 15) / 16, mbh = (frames[i].height + 15) / 16;
+        L->total_mbs += mbw * mbh;
+        if (mbw * mbh > L->max_mbs) L->max_mbs = mbw * mbh;
+    }
+    if (L->total_mbs > (1ll << 28)) return SKMMSE_ERR_SHAPE;
+    size_t off = 0;
+    L->o_frames = off; off = align_up(off + sizeof(FrameDev) * n, 128);
+    L->o_tmaps = off; off = align_up(off + sizeof(CUtensorMap) * n, 128);
+    L->stage_bytes = off;  // frames + tensor maps come from the host
+    L->o_eom = off; off = align_up(off + sizeof(int) * L->total_mbs, 128);
+    L->o_ent = off; off = align_up(off + sizeof(int4) * L->total_mbs, 128);
+    L->o_done = off; off = align_up(off + sizeof(unsigned) * L->total_mbs, 128);
+    L->o_vals = off; off = align_up(off + sizeof(float) * 256 * L->total_mbs, 128);
+    L->o_lev = off; off = align_up(off + sizeof(int) * L->total_mbs, 128);
+    L->o_hist = off; off = align_up(off + sizeof(int) * 2 * L->max_mbs, 128);  // hist + cursor
+    L->need = off;
+    return SKMMSE_OK;
+}
+
+void fill_descriptors(PFN_cuTensorMapEncodeTiled_v12000 encode, const skmmse_frame* frames, int n,
+                      const skmmse_params* p, const BatchLayout& L, unsigned char* host) {
+    FrameDev* hf = reinterpret_cast<FrameDev*>(host + L.o_frames);
+    CUtensorMap* ht = reinterpret_cast<CUtensorMap*>(host + L.o_tmaps);
+    long long mb_base = 0;
+    for (int i = 0; i < n; ++i) {
+        const skmmse_frame& f = frames[i];
+        FrameDev& d = hf[i];
+        std::memset(&d, 0, sizeof(d));
+        d.in = f.frame;
+        d.out = f.out;
+        d.out_f32 = f.out_f32;
+        d.lost = f.mb_lost;
+        d.trace = (p->flags & SKMMSE_FLAG_TRACE) ? f.trace : nullptr;
+        d.w = f.width;
+        d.h = f.height;
+        d.pitch = f.pitch;
+        d.out_pitch = f.out_pitch;
+        d.out_f32_pitch = f.out_f32 ? f.out_f32_pitch : 0;
+        d.mbw = (f.width + 15) / 16;
+        d.mbh = (f.height + 15) / 16;
+        d.mb_base = (int)mb_base;
+        mb_base += (long long)d.mbw * d.mbh;
+        std::memset(&ht[i], 0, sizeof(CUtensorMap));
+        d.use_tma = 0;
+        const bool aligned = (reinterpret_cast<uintptr_t>(f.frame) % 16 == 0) && (f.pitch % 16 == 0);
+        if (encode && aligned) {
+            cuuint64_t gdim[2] = {(cuuint64_t)f.width, (cuuint64_t)f.height};
+            cuuint64_t gstride[1] = {(cuuint64_t)f.pitch};
+            cuuint32_t box[2] = {(cuuint32_t)sk::kReg, (cuuint32_t)sk::kReg};
+            cuuint32_t estr[2] = {1, 1};
+            CUresult r = encode(&ht[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(f.frame),
+                                gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            d.use_tma = (r == CUDA_SUCCESS) ? 1 : 0;
+        }
+    }
+}
+
+// the device work of one batch call, in stream order (capturable): received pixels to the
+// outputs, counters cleared, queue built, persistent concealment kernel
+skmmse_status enqueue_batch(const skmmse_frame* frames, int n, const BatchLayout& L,
+                            unsigned char* arena, int* counters, unsigned long long* stats,
+                            const KParams& kp, long long grid, cudaStream_t stream) {
+    for (int i = 0; i < n; ++i) {
+        const skmmse_frame& f = frames[i];
+        if (f.out != f.frame)
+            SK_CHECK(cudaMemcpy2DAsync(f.out, f.out_pitch, f.frame, f.pitch, f.width, f.height,
+                                       cudaMemcpyDeviceToDevice, stream));
+    }
+    SK_CHECK(cudaMemsetAsync(counters, 0, 4 * sizeof(int), stream));
+    SK_CHECK(cudaMemsetAsync(stats, 0, sk::kNStats * sizeof(unsigned long long), stream));
+    SK_CHECK(cudaMemsetAsync(arena + L.o_hist, 0, sizeof(int) * 2 * L.max_mbs, stream));
+    WorkDev w;
+    w.frames = reinterpret_cast<const FrameDev*>(arena + L.o_frames);
+    w.tmaps = reinterpret_cast<const CUtensorMap*>(arena + L.o_tmaps);
+    w.nframes = n;
+    w.entry_of_mb = reinterpret_cast<int*>(arena + L.o_eom);
+    w.entries = reinterpret_cast<int4*>(arena + L.o_ent);
+    w.counters = counters;
+    w.done = reinterpret_cast<unsigned*>(arena + L.o_done);
+    w.vals = reinterpret_cast<float*>(arena + L.o_vals);
+    w.stats = stats;
+    w.level_of_mb = reinterpret_cast<int*>(arena + L.o_lev);
+    w.lvl_hist = reinterpret_cast<int*>(arena + L.o_hist);
+    w.lvl_cursor = w.lvl_hist + L.max_mbs;
+    w.nlev = (int)L.max_mbs;
+    sk::queue_levels_kernel<<<n, sk::kThreads, 0, stream>>>(w, kp.concealed_is_support);
+    sk::queue_offsets_kernel<<<1, sk::kThreads, 0, stream>>>(w);
+    sk::queue_fill_kernel<<<n, sk::kThreads, 0, stream>>>(w);
+    SK_CHECK(cudaGetLastError());
+    if (grid > L.total_mbs) grid = L.total_mbs;
+    if (grid < 1) grid = 1;
+    sk::conceal_kernel<<<(unsigned)grid, sk::kThreads, sizeof(sk::Smem), stream>>>(w, kp);
+    SK_CHECK(cudaGetLastError());
+    return SKMMSE_OK;
+}
+
+skmmse_status read_stats_from(const unsigned long long* d_stats, const int* d_counters,
+                              long long nbeta, skmmse_stats* h, cudaStream_t stream) {
+    unsigned long long raw[sk::kNStats];
+    int counters[4];
+    SK_CHECK(cudaMemcpyAsync(raw, d_stats, sizeof(raw), cudaMemcpyDeviceToHost, stream));
+    SK_CHECK(cudaMemcpyAsync(counters, d_counters, sizeof(counters), cudaMemcpyDeviceToHost, stream));
+    SK_CHECK(cudaStreamSynchronize(stream));
+    std::memset(h, 0, sizeof(*h));
+    long long* dst = &h->n_lost_mbs;
+    for (int i = 0; i < sk::ST_COUNT; ++i) dst[i] = (long long)raw[i];
+    h->n_beta = nbeta;
+    h->error = counters[2];
+    return counters[2] ? SKMMSE_ERR_TIMEOUT : SKMMSE_OK;
 }
 
 // ------------------------------------------------------------------------------------
@@ -283,131 +414,165 @@ skmmse_status skmmse_conceal_batch(skmmse_context* c, const skmmse_frame* frames
                                    const skmmse_params* p, skmmse_stats* h_stats,
                                    void* stream_v) {
     if (!c || !frames || n < 1) return n < 1 && c && frames ? SKMMSE_ERR_SHAPE : SKMMSE_ERR_ARG;
-    if (n > 65536) return SKMMSE_ERR_SHAPE;
-    skmmse_status s = validate_params(p);
+    BatchLayout L;
+    skmmse_status s = plan_batch(frames, n, p, &L);
     if (s != SKMMSE_OK) return s;
-    long long total_mbs = 0, max_mbs = 1;
-    for (int i = 0; i < n; ++i) {
-        s = validate_frame(frames[i]);
-        if (s != SKMMSE_OK) return s;
-        const long long mbw = (frames[i].width + 15) / 16, mbh = (frames[i].height + 15) / 16;
-        total_mbs += mbw * mbh;
-        if (mbw * mbh > max_mbs) max_mbs = mbw * mbh;
-    }
-    if (total_mbs > (1ll << 28)) return SKMMSE_ERR_SHAPE;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
-
-    // arena layout
-    size_t off = 0;
-    const size_t o_frames = off; off = align_up(off + sizeof(FrameDev) * n, 128);
-    const size_t o_tmaps = off; off = align_up(off + sizeof(CUtensorMap) * n, 128);
-    const size_t o_eom = off; off = align_up(off + sizeof(int) * total_mbs, 128);
-    const size_t o_ent = off; off = align_up(off + sizeof(int4) * total_mbs, 128);
-    const size_t o_done = off; off = align_up(off + sizeof(unsigned) * total_mbs, 128);
-    const size_t o_vals = off; off = align_up(off + sizeof(float) * 256 * total_mbs, 128);
-    const size_t o_lev = off; off = align_up(off + sizeof(int) * total_mbs, 128);
-    const size_t o_hist = off; off = align_up(off + sizeof(int) * 2 * max_mbs, 128);  // hist + cursor
-    const size_t need = off;
-    if (need > c->arena_bytes) {
+    if (L.need > c->arena_bytes) {
         if (c->stage_pending) cudaEventSynchronize(c->stage_done);
         SK_CHECK(cudaStreamSynchronize(stream));
         if (c->d_arena) cudaFree(c->d_arena);
         c->d_arena = nullptr;
         c->arena_bytes = 0;
-        SK_CHECK(cudaMalloc(&c->d_arena, need));
-        c->arena_bytes = need;
+        SK_CHECK(cudaMalloc(&c->d_arena, L.need));
+        c->arena_bytes = L.need;
     }
-    const size_t stage_need = o_eom;  // frames + tmaps
-    if (stage_need > c->h_stage_bytes) {
+    if (L.stage_bytes > c->h_stage_bytes) {
         if (c->stage_pending) cudaEventSynchronize(c->stage_done);
         if (c->h_stage) cudaFreeHost(c->h_stage);
         c->h_stage = nullptr;
         c->h_stage_bytes = 0;
-        SK_CHECK(cudaMallocHost(&c->h_stage, stage_need));
-        c->h_stage_bytes = stage_need;
+        SK_CHECK(cudaMallocHost(&c->h_stage, L.stage_bytes));
+        c->h_stage_bytes = L.stage_bytes;
     }
     if (c->stage_pending) {  // the previous call's upload must have left the staging area
         SK_CHECK(cudaEventSynchronize(c->stage_done));
         c->stage_pending = false;
     }
-    FrameDev* hf = reinterpret_cast<FrameDev*>(c->h_stage + o_frames);
-    CUtensorMap* ht = reinterpret_cast<CUtensorMap*>(c->h_stage + o_tmaps);
-    long long mb_base = 0;
-    for (int i = 0; i < n; ++i) {
-        const skmmse_frame& f = frames[i];
-        FrameDev& d = hf[i];
-        std::memset(&d, 0, sizeof(d));
-        d.in = f.frame;
-        d.out = f.out;
-        d.out_f32 = f.out_f32;
-        d.lost = f.mb_lost;
-        d.trace = (p->flags & SKMMSE_FLAG_TRACE) ? f.trace : nullptr;
-        d.w = f.width;
-        d.h = f.height;
-        d.pitch = f.pitch;
-        d.out_pitch = f.out_pitch;
-        d.out_f32_pitch = f.out_f32 ? f.out_f32_pitch : 0;
-        d.mbw = (f.width + 15) / 16;
-        d.mbh = (f.height + 15) / 16;
-        d.mb_base = (int)mb_base;
-        mb_base += (long long)d.mbw * d.mbh;
-        std::memset(&ht[i], 0, sizeof(CUtensorMap));
-        d.use_tma = 0;
-        const bool aligned = (reinterpret_cast<uintptr_t>(f.frame) % 16 == 0) && (f.pitch % 16 == 0);
-        if (c->encode && aligned) {
-            cuuint64_t gdim[2] = {(cuuint64_t)f.width, (cuuint64_t)f.height};
-            cuuint64_t gstride[1] = {(cuuint64_t)f.pitch};
-            cuuint32_t box[2] = {(cuuint32_t)sk::kReg, (cuuint32_t)sk::kReg};
-            cuuint32_t estr[2] = {1, 1};
-            CUresult r = c->encode(&ht[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
-                                   const_cast<uint8_t*>(f.frame), gdim, gstride, box, estr,
-                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            d.use_tma = (r == CUDA_SUCCESS) ? 1 : 0;
-        }
-    }
-    // received pixels -> out
-    for (int i = 0; i < n; ++i) {
-        const skmmse_frame& f = frames[i];
-        if (f.out != f.frame)
-            SK_CHECK(cudaMemcpy2DAsync(f.out, f.out_pitch, f.frame, f.pitch, f.width, f.height,
-                                       cudaMemcpyDeviceToDevice, stream));
-    }
-    SK_CHECK(cudaMemcpyAsync(c->d_arena, c->h_stage, stage_need, cudaMemcpyHostToDevice, stream));
+    fill_descriptors(c->encode, frames, n, p, L, c->h_stage);
+    SK_CHECK(cudaMemcpyAsync(c->d_arena, c->h_stage, L.stage_bytes, cudaMemcpyHostToDevice, stream));
     SK_CHECK(cudaEventRecord(c->stage_done, stream));
     c->stage_pending = true;
-    SK_CHECK(cudaMemsetAsync(c->d_counters, 0, 4 * sizeof(int), stream));
-    SK_CHECK(cudaMemsetAsync(c->d_stats, 0, sk::kNStats * sizeof(unsigned long long), stream));
-    SK_CHECK(cudaMemsetAsync(c->d_arena + o_hist, 0, sizeof(int) * 2 * max_mbs, stream));
-
-    WorkDev w;
-    w.frames = reinterpret_cast<const FrameDev*>(c->d_arena + o_frames);
-    w.tmaps = reinterpret_cast<const CUtensorMap*>(c->d_arena + o_tmaps);
-    w.nframes = n;
-    w.entry_of_mb = reinterpret_cast<int*>(c->d_arena + o_eom);
-    w.entries = reinterpret_cast<int4*>(c->d_arena + o_ent);
-    w.counters = c->d_counters;
-    w.done = reinterpret_cast<unsigned*>(c->d_arena + o_done);
-    w.vals = reinterpret_cast<float*>(c->d_arena + o_vals);
-    w.stats = c->d_stats;
-    w.level_of_mb = reinterpret_cast<int*>(c->d_arena + o_lev);
-    w.lvl_hist = reinterpret_cast<int*>(c->d_arena + o_hist);
-    w.lvl_cursor = w.lvl_hist + max_mbs;
-    w.nlev = (int)max_mbs;
     const KParams kp = make_kparams(p);
     c->last_nbeta = kp.nbeta;
-
-    sk::queue_levels_kernel<<<n, sk::kThreads, 0, stream>>>(w, kp.concealed_is_support);
-    sk::queue_offsets_kernel<<<1, sk::kThreads, 0, stream>>>(w);
-    sk::queue_fill_kernel<<<n, sk::kThreads, 0, stream>>>(w);
-    SK_CHECK(cudaGetLastError());
-    long long grid = (long long)c->sm_count * c->blocks_per_sm;
-    if (grid > total_mbs) grid = total_mbs;
-    if (grid < 1) grid = 1;
-    sk::conceal_kernel<<<(unsigned)grid, sk::kThreads, c->smem_bytes, stream>>>(w, kp);
-    SK_CHECK(cudaGetLastError());
+    const long long grid = (long long)c->sm_count * (c->ctas_per_sm > 0 ? c->ctas_per_sm : c->blocks_per_sm);
+    s = enqueue_batch(frames, n, L, c->d_arena, c->d_counters, c->d_stats, kp, grid, stream);
+    if (s != SKMMSE_OK) return s;
     if (h_stats) return skmmse_read_stats(c, h_stats, stream_v);
+    return SKMMSE_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// CUDA graph of a batch call on fixed frame buffers
+
+struct skmmse_graph {
+    unsigned char* d_arena = nullptr;
+    int* d_counters = nullptr;
+    unsigned long long* d_stats = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long nbeta = 0;
+};
+
+void skmmse_graph_destroy(skmmse_graph* g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->d_arena) cudaFree(g->d_arena);
+    if (g->d_counters) cudaFree(g->d_counters);
+    if (g->d_stats) cudaFree(g->d_stats);
+    delete g;
+}
+
+skmmse_status skmmse_graph_create(skmmse_context* c, const skmmse_frame* frames, int n,
+                                  const skmmse_params* p, skmmse_graph** out) {
+    if (!c || !frames || !out || n < 1) return SKMMSE_ERR_ARG;
+    *out = nullptr;
+    BatchLayout L;
+    skmmse_status s = plan_batch(frames, n, p, &L);
+    if (s != SKMMSE_OK) return s;
+    skmmse_graph* g = new (std::nothrow) skmmse_graph();
+    if (!g) return SKMMSE_ERR_NOMEM;
+    std::vector<unsigned char> host(L.stage_bytes);
+    fill_descriptors(c->encode, frames, n, p, L, host.data());
+    const KParams kp = make_kparams(p);
+    g->nbeta = kp.nbeta;
+    const long long grid = (long long)c->sm_count * (c->ctas_per_sm > 0 ? c->ctas_per_sm : c->blocks_per_sm);
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaMalloc(&g->d_arena, L.need);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_counters, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_stats, sk::kNStats * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_arena, host.data(), L.stage_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        s = enqueue_batch(frames, n, L, g->d_arena, g->d_counters, g->d_stats, kp, grid, cs);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        g->graph = graph;
+        if (s == SKMMSE_OK && e2 != cudaSuccess) s = cuda_fail(e2);
+        if (s == SKMMSE_OK) {
+            e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+            if (e != cudaSuccess) s = cuda_fail(e);
+        }
+    } else {
+        s = cuda_fail(e);
+    }
+    if (cs) cudaStreamDestroy(cs);
+    if (s != SKMMSE_OK) {
+        skmmse_graph_destroy(g);
+        return s;
+    }
+    *out = g;
+    return SKMMSE_OK;
+}
+
+skmmse_status skmmse_graph_launch(skmmse_graph* g, void* stream) {
+    if (!g || !g->exec) return SKMMSE_ERR_ARG;
+    SK_CHECK(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+    return SKMMSE_OK;
+}
+
+skmmse_status skmmse_graph_read_stats(skmmse_graph* g, skmmse_stats* h, void* stream_v) {
+    if (!g || !h) return SKMMSE_ERR_ARG;
+    return read_stats_from(g->d_stats, g->d_counters, g->nbeta, h, static_cast<cudaStream_t>(stream_v));
+}
+
+// ------------------------------------------------------------------------------------
+// autotuner: the persistent grid size
+
+skmmse_status skmmse_autotune(skmmse_context* c, const skmmse_frame* frames, int n,
+                              const skmmse_params* p, int reps, void* stream_v,
+                              float* h_ms_per_option, int* h_best) {
+    if (!c || !frames || n < 1 || reps < 1) return SKMMSE_ERR_ARG;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    cudaEvent_t a = nullptr, b = nullptr;
+    SK_CHECK(cudaEventCreate(&a));
+    SK_CHECK(cudaEventCreate(&b));
+    const int saved = c->ctas_per_sm;
+    float best = 1e30f;
+    int best_k = c->blocks_per_sm;
+    skmmse_status s = SKMMSE_OK;
+    for (int k = 1; k <= c->blocks_per_sm && s == SKMMSE_OK; ++k) {
+        c->ctas_per_sm = k;
+        s = skmmse_conceal_batch(c, frames, n, p, nullptr, stream_v);  // warm-up
+        float tot = 0.0f;
+        for (int r = 0; r < reps && s == SKMMSE_OK; ++r) {
+            cudaEventRecord(a, stream);
+            s = skmmse_conceal_batch(c, frames, n, p, nullptr, stream_v);
+            cudaEventRecord(b, stream);
+            if (cudaEventSynchronize(b) != cudaSuccess) s = SKMMSE_ERR_CUDA;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, a, b);
+            tot += ms;
+        }
+        const float avg = tot / reps;
+        if (h_ms_per_option && k <= 8) h_ms_per_option[k - 1] = avg;
+        if (avg < best) {
+            best = avg;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    c->ctas_per_sm = (s == SKMMSE_OK) ? best_k : saved;
+    if (h_best) *h_best = c->ctas_per_sm;
+    return s;
+}
+
+skmmse_status skmmse_set_ctas_per_sm(skmmse_context* c, int k) {
+    if (!c || k < 0 || k > c->blocks_per_sm) return SKMMSE_ERR_ARG;
+    c->ctas_per_sm = k;
     return SKMMSE_OK;
 }
 
@@ -431,18 +596,7 @@ skmmse_status skmmse_conceal(skmmse_context* c, const uint8_t* d_frame, int widt
 
 skmmse_status skmmse_read_stats(skmmse_context* c, skmmse_stats* h, void* stream_v) {
     if (!c || !h) return SKMMSE_ERR_ARG;
-    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
-    unsigned long long raw[sk::kNStats];
-    int counters[4];
-    SK_CHECK(cudaMemcpyAsync(raw, c->d_stats, sizeof(raw), cudaMemcpyDeviceToHost, stream));
-    SK_CHECK(cudaMemcpyAsync(counters, c->d_counters, sizeof(counters), cudaMemcpyDeviceToHost, stream));
-    SK_CHECK(cudaStreamSynchronize(stream));
-    std::memset(h, 0, sizeof(*h));
-    long long* dst = &h->n_lost_mbs;
-    for (int i = 0; i < sk::ST_COUNT; ++i) dst[i] = (long long)raw[i];
-    h->n_beta = c->last_nbeta;
-    h->error = counters[2];
-    return counters[2] ? SKMMSE_ERR_TIMEOUT : SKMMSE_OK;
+    return read_stats_from(c->d_stats, c->d_counters, c->last_nbeta, h, static_cast<cudaStream_t>(stream_v));
 }
 
 skmmse_status skmmse_conceal_noalloc(const uint8_t* d_frame, int width, int height, int pitch,

@@ -72,7 +72,9 @@ TRACE_DTYPE = np.dtype([
 # every symbol include/skmmse.h declares
 EXPORTS = ["skmmse_abi_version", "skmmse_struct_size", "skmmse_status_str", "skmmse_params_preset",
            "skmmse_create", "skmmse_destroy", "skmmse_conceal", "skmmse_conceal_batch",
-           "skmmse_read_stats", "skmmse_read_phase_clocks", "skmmse_conceal_noalloc"]
+           "skmmse_read_stats", "skmmse_read_phase_clocks", "skmmse_conceal_noalloc",
+           "skmmse_graph_create", "skmmse_graph_launch", "skmmse_graph_read_stats",
+           "skmmse_graph_destroy", "skmmse_autotune", "skmmse_set_ctas_per_sm"]
 
 _lib = None
 
@@ -114,6 +116,20 @@ def load(path: str = LIB_PATH):
     lib.skmmse_conceal_noalloc.restype = ci
     lib.skmmse_conceal_noalloc.argtypes = [vp, ci, ci, ci, vp, ctypes.POINTER(Params), vp, ci, vp,
                                            ctypes.POINTER(Stats), vp]
+    lib.skmmse_graph_create.restype = ci
+    lib.skmmse_graph_create.argtypes = [vp, ctypes.POINTER(Frame), ci, ctypes.POINTER(Params),
+                                        ctypes.POINTER(vp)]
+    lib.skmmse_graph_launch.restype = ci
+    lib.skmmse_graph_launch.argtypes = [vp, vp]
+    lib.skmmse_graph_read_stats.restype = ci
+    lib.skmmse_graph_read_stats.argtypes = [vp, ctypes.POINTER(Stats), vp]
+    lib.skmmse_graph_destroy.restype = None
+    lib.skmmse_graph_destroy.argtypes = [vp]
+    lib.skmmse_autotune.restype = ci
+    lib.skmmse_autotune.argtypes = [vp, ctypes.POINTER(Frame), ci, ctypes.POINTER(Params), ci, vp,
+                                    ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ci)]
+    lib.skmmse_set_ctas_per_sm.restype = ci
+    lib.skmmse_set_ctas_per_sm.argtypes = [vp, ci]
     lib.skmmse_read_phase_clocks.restype = ci
     lib.skmmse_read_phase_clocks.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), vp]
     assert lib.skmmse_struct_size(0) == TRACE_DTYPE.itemsize, "trace record layout"
@@ -187,14 +203,9 @@ class Context:
         _check(rc, "skmmse_conceal")
         return out, out_f32, (st.as_dict() if st is not None else None)
 
-    def conceal_batch(self, frames, masks, p: Params | None = None, *, outs=None, outs_f32=None,
-                      traces=None, stats: bool = False, stream=None):
-        """Batch of frames (lists of uint8 CUDA tensors); one persistent launch."""
-        import torch
-        p = p if p is not None else params()
+    @staticmethod
+    def _descs(frames, masks, outs, outs_f32=None, traces=None):
         n = len(frames)
-        if outs is None:
-            outs = [torch.empty_like(f) for f in frames]
         descs = (Frame * n)()
         for i, (f, m) in enumerate(zip(frames, masks)):
             H, W = f.shape
@@ -206,12 +217,45 @@ class Context:
                 d.out_f32, d.out_f32_pitch = outs_f32[i].data_ptr(), outs_f32[i].stride(0)
             if traces is not None and traces[i] is not None:
                 d.trace = traces[i].data_ptr()
+        return descs
+
+    def conceal_batch(self, frames, masks, p: Params | None = None, *, outs=None, outs_f32=None,
+                      traces=None, stats: bool = False, stream=None):
+        """Batch of frames (lists of uint8 CUDA tensors); one persistent launch."""
+        import torch
+        p = p if p is not None else params()
+        n = len(frames)
+        if outs is None:
+            outs = [torch.empty_like(f) for f in frames]
+        descs = self._descs(frames, masks, outs, outs_f32, traces)
         st = Stats() if stats else None
         rc = self._lib.skmmse_conceal_batch(self._h, descs, n, ctypes.byref(p),
                                             ctypes.byref(st) if st is not None else None,
                                             _stream_handle(stream))
         _check(rc, "skmmse_conceal_batch")
         return outs, (st.as_dict() if st is not None else None)
+
+    def graph(self, frames, masks, p: Params | None = None, *, outs, outs_f32=None):
+        """Record the batch call on these fixed buffers as a CUDA graph (see Graph)."""
+        return Graph(self, frames, masks, p if p is not None else params(), outs, outs_f32)
+
+    def autotune(self, frames, masks, p: Params | None = None, *, outs=None, reps: int = 2,
+                 stream=None) -> dict:
+        """Pick the persistent CTAs per SM for this batch by timing; returns the timings."""
+        import torch
+        p = p if p is not None else params()
+        if outs is None:
+            outs = [torch.empty_like(f) for f in frames]
+        descs = self._descs(frames, masks, outs)
+        ms = (ctypes.c_float * 8)()
+        best = ctypes.c_int()
+        _check(self._lib.skmmse_autotune(self._h, descs, len(frames), ctypes.byref(p), reps,
+                                         _stream_handle(stream), ms, ctypes.byref(best)),
+               "skmmse_autotune")
+        return {"ctas_per_sm": best.value, "ms": [v for v in ms if v > 0]}
+
+    def set_ctas_per_sm(self, k: int):
+        _check(self._lib.skmmse_set_ctas_per_sm(self._h, int(k)), "skmmse_set_ctas_per_sm")
 
     PHASES = ["stage", "ctx", "brl", "idl", "h_cand", "h_cov", "h_chol", "h_dist", "h_beta",
               "h_i0", "h_alpha", "h_est", "writeback", "publish"]
@@ -229,6 +273,42 @@ class Context:
         d = st.as_dict()
         d["status"] = rc
         return d
+
+
+class Graph:
+    """A batch call on fixed device buffers captured as a CUDA graph: each launch()
+    conceals what the frame buffers hold at that time (persistent kernel and queue
+    construction replayed without host work)."""
+
+    def __init__(self, ctx: Context, frames, masks, p: Params, outs, outs_f32=None):
+        self._lib = ctx._lib
+        self._keep = (frames, masks, outs, outs_f32)  # the buffers must outlive the graph
+        descs = Context._descs(frames, masks, outs, outs_f32)
+        h = ctypes.c_void_p()
+        _check(self._lib.skmmse_graph_create(ctx._h, descs, len(frames), ctypes.byref(p),
+                                             ctypes.byref(h)), "skmmse_graph_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(self._lib.skmmse_graph_launch(self._h, _stream_handle(stream)), "skmmse_graph_launch")
+
+    def read_stats(self, stream=None) -> dict:
+        st = Stats()
+        rc = self._lib.skmmse_graph_read_stats(self._h, ctypes.byref(st), _stream_handle(stream))
+        d = st.as_dict()
+        d["status"] = rc
+        return d
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.skmmse_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def trace_buffer(mb_lost_np: np.ndarray, device="cuda"):

@@ -56,6 +56,24 @@ def parse():
     return ap.parse_args()
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Replicas: every rank conceals its own seeded batch (no data exchange)."""
+    return seed + 1000 * rank
+
+
+def reduce_over_ranks(dist, total_ms: float, e2e_ms: float, n_units: int, device):
+    """Whole-job figures of a replicated run: the slowest rank's times (max over ranks) and
+    the units all ranks processed (sum).  `dist` is torch.distributed or None (one rank)."""
+    if dist is None:
+        return float(total_ms), float(e2e_ms), float(n_units)
+    import torch
+    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(n_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), float(u[0])
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -210,7 +228,7 @@ def run_ours(args):
         dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
     skbuild.build()
     from paper_2205_11226_gb300 import skmmse
-    frames, masks = build_workload(args.seed + 1000 * rank, args.workload)
+    frames, masks = build_workload(rank_seed(args.seed, rank), args.workload)
     p = skmmse.params(args.profile)
     ctx = skmmse.Context()
     stream = torch.cuda.current_stream()
@@ -284,16 +302,7 @@ def run_ours(args):
                               frames[i][~np.kron(masks[i].astype(bool), np.ones((16, 16), bool))[:frames[i].shape[0], :frames[i].shape[1]]])
                for i in range(0, len(frames), 16))
 
-    # max over ranks
-    tot = torch.tensor([total_ms, e2e_ms, float(n_lost)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        mx = tot.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tot.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        total_ms, e2e_ms, units = float(mx[0]), float(mx[1]), float(sm[2])
-    else:
-        units = float(n_lost)
+    total_ms, e2e_ms, units = reduce_over_ranks(dist, total_ms, e2e_ms, n_lost, "cuda")
     value = units * args.steps / (total_ms * 1e-3)
     e2e_value = units * args.steps / (e2e_ms * 1e-3)
 

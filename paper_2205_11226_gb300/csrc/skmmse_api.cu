@@ -65,11 +65,9 @@ skmmse_status validate_params(const skmmse_params* p) {
     if (p->ring_step < 1 || p->ring_step > 64) return SKMMSE_ERR_ARG;
     const int nb = p->beta_kmax - p->beta_kmin + 1;
     if (nb < 1 || nb > sk::kMaxBeta || p->beta_kmin < -60 || p->beta_kmax > 60) return SKMMSE_ERR_ARG;
-    if (p->precision != SKMMSE_FP32) {
-        if (p->precision == SKMMSE_MIXED_BF16 || p->precision == SKMMSE_MIXED_FP16)
-            return SKMMSE_ERR_UNSUPPORTED;
+    if (p->precision != SKMMSE_FP32 && p->precision != SKMMSE_MIXED_BF16 &&
+        p->precision != SKMMSE_MIXED_FP16)
         return SKMMSE_ERR_ARG;
-    }
     if (p->flags & ~(SKMMSE_FLAG_TRACE | SKMMSE_FLAG_FORCE)) return SKMMSE_ERR_ARG;
     if ((p->flags & SKMMSE_FLAG_FORCE) && !(p->flags & SKMMSE_FLAG_TRACE)) return SKMMSE_ERR_ARG;
     return SKMMSE_OK;
@@ -105,9 +103,33 @@ KParams make_kparams(const skmmse_params* p) {
     }
     k.concealed_is_support = p->concealed_is_support ? 1 : 0;
     k.flags = p->flags;
+    k.mixed = p->precision;
     return k;
 }
 
+
+// ------------------------------------------------------------------------------------
+// kernel instantiations: FP32, and tensor-core contractions with BF16 or FP16 operands
+
+void launch_conceal(const KParams& kp, const WorkDev& w, unsigned grid, cudaStream_t stream) {
+    if (kp.mixed == 1)
+        sk::conceal_kernel<1><<<grid, sk::kThreads, sizeof(sk::Smem), stream>>>(w, kp);
+    else if (kp.mixed == 2)
+        sk::conceal_kernel<2><<<grid, sk::kThreads, sizeof(sk::Smem), stream>>>(w, kp);
+    else
+        sk::conceal_kernel<0><<<grid, sk::kThreads, sizeof(sk::Smem), stream>>>(w, kp);
+}
+
+cudaError_t set_kernel_attributes() {
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sk::conceal_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(sk::Smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sk::conceal_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(sk::Smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sk::conceal_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(sk::Smem));
+    return e;
+}
 
 // ------------------------------------------------------------------------------------
 // batch planning shared by direct calls and graph capture
@@ -218,7 +240,7 @@ skmmse_status enqueue_batch(const skmmse_frame* frames, int n, const BatchLayout
     SK_CHECK(cudaGetLastError());
     if (grid > L.total_mbs) grid = L.total_mbs;
     if (grid < 1) grid = 1;
-    sk::conceal_kernel<<<(unsigned)grid, sk::kThreads, sizeof(sk::Smem), stream>>>(w, kp);
+    launch_conceal(kp, w, (unsigned)grid, stream);
     SK_CHECK(cudaGetLastError());
     return SKMMSE_OK;
 }
@@ -296,11 +318,9 @@ skmmse_status noalloc_setup(int dev, NoAllocDevice** out) {
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || ptr == nullptr) return cuda_fail(e);
         e = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = set_kernel_attributes();
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(sk::conceal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sizeof(sk::Smem));
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, sk::conceal_kernel,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, sk::conceal_kernel<0>,
                                                               sk::kThreads, sizeof(sk::Smem));
         if (e != cudaSuccess || d.blocks_per_sm < 1) return cuda_fail(e);
         void* fn = nullptr;
@@ -373,11 +393,9 @@ skmmse_status skmmse_create(skmmse_context** out) {
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
     c->smem_bytes = sizeof(sk::Smem);
+    if (e == cudaSuccess) e = set_kernel_attributes();
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sk::conceal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)c->smem_bytes);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm, sk::conceal_kernel,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->blocks_per_sm, sk::conceal_kernel<0>,
                                                           sk::kThreads, c->smem_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_stats, sk::kNStats * sizeof(unsigned long long));
@@ -684,7 +702,7 @@ skmmse_status skmmse_conceal_noalloc(const uint8_t* d_frame, int width, int heig
     long long grid = (long long)nd->sm_count * nd->blocks_per_sm;
     if (grid > mbw * mbh) grid = mbw * mbh;
     if (grid < 1) grid = 1;
-    sk::conceal_kernel<<<(unsigned)grid, sk::kThreads, sizeof(sk::Smem), stream>>>(w, kp);
+    launch_conceal(kp, w, (unsigned)grid, stream);
     SK_CHECK(cudaGetLastError());
     if (h_stats) {
         unsigned long long raw[sk::kNStats];

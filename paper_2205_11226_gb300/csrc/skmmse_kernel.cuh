@@ -23,7 +23,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "df.cuh"
+#include "tc.cuh"
 
 namespace sk {
 
@@ -88,6 +92,7 @@ struct KParams {
     float inv2beta[kMaxBeta];  // 1 / (2 beta_b), beta_b = 2^((kmin+b)/2)
     int concealed_is_support;
     unsigned flags;
+    int mixed;            // 0: FP32 on the CUDA cores; 1: BF16, 2: FP16 tensor-core contractions
 };
 
 struct FrameDev {
@@ -152,7 +157,6 @@ struct __align__(16) HqlP2 {                 // beta / leave-one-out phase
 struct __align__(16) Hql {
     uint16_t cand[kNcand + 7];  // window top-left as S offset u*48+v
     float d[kNcand + 7];
-    __align__(16) float Z[2][kCh][kZs];  // staged candidates, centred by the integer shift
     __align__(16) float Linv[32][36];
     float G[4][32];
     df32 cxy[4][32];            // C_XY (double-float)
@@ -177,8 +181,19 @@ struct __align__(16) Hql {
     float lam;
     float alpha;
     union {
-        HqlP1 p1;
-        HqlP2 p2;
+        struct {  // CUDA-core staging and phase buffers
+            __align__(16) float Z[2][kCh][kZs];  // staged candidates, centred by the integer shift
+            union {
+                HqlP1 p1;
+                HqlP2 p2;
+            };
+        };
+        struct {  // tensor-core operand tiles: 128 rows x 64 16-bit columns, K-major, no swizzle
+            __align__(16) uint16_t t0[128 * 64];
+            __align__(16) uint16_t t1[128 * 64];
+            __align__(16) uint16_t t2[128 * 64];
+            __align__(16) uint16_t t3[128 * 64];
+        } mx;
     };
 };
 
@@ -201,6 +216,9 @@ struct __align__(128) Smem {
     unsigned long long st[kNStats];    // per-CTA counters
     TraceRec tr;                       // trace record of the current step
     long long ph_t;                    // last phase mark (SKMMSE_PHASE_CLOCKS)
+    uint64_t mma_bar;                  // tensor-core completion (mixed precision)
+    unsigned tmem_base;                // tensor memory of this CTA (mixed precision)
+    int mma_err;
     union {
         IdlSlot idl[2][kWarps];
         Hql hql;
@@ -388,9 +406,33 @@ constexpr float kNegBig = -1.0e30f;
 // ------------------------------------------------------------------------------------
 // IDL: Eq. (15) over growing rings; returns 1 accepted, 0 not accepted, -1 no candidate
 
-__device__ __forceinline__ int idl_step(Smem& sm, const KParams& P, const StepCtx& c, float xhat[4],
-                        int* ring_out, float* lognu_out, long long* evals) {
+// Not inlined, with scalar arguments: the 36 context values live in registers only while
+// this function runs, so the per-step loop of the kernel keeps a small register footprint.
+struct IdlOut {
+    float x[4];
+    float lognu;
+    int ring;
+    int evals;  // candidates evaluated (thread 0)
+    int r;      // 1 accepted, 0 not accepted, -1 no candidate
+};
+
+__device__ __noinline__ IdlOut idl_step(Smem& sm, const KParams& P, int wr, int wc,
+                                        unsigned long long ymask, int ny, float mean) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    StepCtx c;
+    c.wr = wr;
+    c.wc = wc;
+    c.ymask = ymask;
+    c.ny = ny;
+    c.mean = mean;
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+        c.rowcfg[r] = (unsigned)((ymask >> (6 * r)) & 63ull) | ((r == 2 || r == 3) ? 12u : 0u);
+#pragma unroll
+    for (int k = 0; k < 36; ++k) c.y0w[k] = sm.S[(wr + k / 6) * kReg + wc + k % 6];
+    IdlOut out;
+    float* xhat = out.x;
+    xhat[0] = xhat[1] = xhat[2] = xhat[3] = mean;
     const int pr = c.wr + 2, pc = c.wc + 2;  // patch top-left (region)
     const float inv_h = P.inv_2sig2 / (float)c.ny;
     const float cen = rintf(c.mean);
@@ -458,11 +500,11 @@ __device__ __forceinline__ int idl_step(Smem& sm, const KParams& P, const StepCt
             }
         }
     }
-    if (tid == 0) *evals = total_cnt;
-    *ring_out = accepted ? k : P.nrings;
-    *lognu_out = lognu;
-    if (total_cnt == 0) return -1;
-    return accepted;
+    out.evals = total_cnt;
+    out.ring = accepted ? k : P.nrings;
+    out.lognu = lognu;
+    out.r = total_cnt == 0 ? -1 : accepted;
+    return out;
 }
 
 // ------------------------------------------------------------------------------------
@@ -546,18 +588,259 @@ __device__ __forceinline__ void whiten_tile(const Hql& h, int buf, int ny, int t
     }
 }
 
-__device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepCtx& c, float xhat[4],
-                                         TraceRec* tr, bool trace) {
+// ------------------------------------------------------------------------------------
+// Mixed precision: the HQL contractions on tcgen05 tensor cores.  Operands are split into
+// two 16-bit parts, v ~ hi + lo (BF16: ~16 significant bits; FP16: ~22), and every product
+// is accumulated as hi*hi + hi*lo + lo*hi in FP32 tensor memory.
+
+template <bool BF16>
+__device__ __forceinline__ void split16(float v, uint16_t& hi, uint16_t& lo) {
+    if (BF16) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi = __bfloat16_as_ushort(h);
+        lo = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+    } else {
+        const __half h = __float2half_rn(v);
+        hi = __half_as_ushort(h);
+        lo = __half_as_ushort(__float2half_rn(v - __half2float(h)));
+    }
+}
+
+// 8 consecutive K elements of row r of a K-major tile with K columns: one 16-byte row of a
+// core matrix in each of the hi and lo tiles
+template <bool BF16>
+__device__ __forceinline__ void store8_split(uint16_t* thi, uint16_t* tlo, int r, int k0, int K,
+                                             const float v[8]) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint16_t h0, l0, h1, l1;
+        split16<BF16>(v[2 * q], h0, l0);
+        split16<BF16>(v[2 * q + 1], h1, l1);
+        h[q] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+        l[q] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+    }
+    const uint32_t off = tc::kmajor_offset(r, k0, K) >> 1;  // in 16-bit elements
+    *reinterpret_cast<uint4*>(thi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(tlo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ void zero_tiles(Hql& h) {
+    uint4* p = reinterpret_cast<uint4*>(&h.mx);
+    for (int i = threadIdx.x; i < (int)(sizeof(h.mx) / 16); i += kThreads) p[i] = make_uint4(0, 0, 0, 0);
+}
+
+// D (+)= A * B^T over K columns with split operands (issued by one thread)
+__device__ __forceinline__ void mma3(uint32_t tmem, const uint16_t* ahi, const uint16_t* alo,
+                                     const uint16_t* bhi, const uint16_t* blo, int K, uint32_t idesc,
+                                     bool accumulate) {
+    const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+    const uint32_t a0 = tc::smem_addr(ahi), a1 = tc::smem_addr(alo);
+    const uint32_t b0 = tc::smem_addr(bhi), b1 = tc::smem_addr(blo);
+    for (int kk = 0; kk < K / 16; ++kk) {
+        const uint32_t o = (uint32_t)kk * 256u;
+        tc::mma_f16(tmem, tc::smem_desc(a0 + o, 128, sbo), tc::smem_desc(b0 + o, 128, sbo), idesc,
+                    accumulate || kk > 0);
+        tc::mma_f16(tmem, tc::smem_desc(a0 + o, 128, sbo), tc::smem_desc(b1 + o, 128, sbo), idesc, true);
+        tc::mma_f16(tmem, tc::smem_desc(a1 + o, 128, sbo), tc::smem_desc(b0 + o, 128, sbo), idesc, true);
+    }
+}
+
+// make the staged tiles visible to the tensor cores, issue (thread 0), wait for completion
+template <typename IssueF>
+__device__ __forceinline__ void mma_round(Smem& sm, uint32_t& mph, IssueF issue) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (threadIdx.x == 0) {
+        issue();
+        tc::mma_commit(&sm.mma_bar);
+    }
+    if (!tc::mbar_wait(&sm.mma_bar, mph, 1u << 26)) atomicExch(&sm.mma_err, 1);
+    mph ^= 1u;
+    tc::fence_after();
+}
+
+// stage rows 0..36 of Z^T for candidates [c0, c0+n): z' (feature rows 0..35, zero beyond
+// nz) and the constant one (row 36)
+template <bool BF16>
+__device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, float shift) {
+    Hql& h = sm.hql;
+    for (int idx = threadIdx.x; idx < 37 * 8; idx += kThreads) {
+        const int a = idx >> 3, g8 = idx & 7;
+        const int ka = a < kZs ? h.koff[a] : -1;
+        float v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int j = 8 * g8 + t;
+            float x = 0.0f;
+            if (j < n) {
+                if (a == 36) x = 1.0f;
+                else if (ka >= 0) x = sm.S[h.cand[c0 + j] + ka] - shift;
+            }
+            v[t] = x;
+        }
+        store8_split<BF16>(h.mx.t0, h.mx.t1, a, 8 * g8, 64, v);
+    }
+}
+
+// H1 on tensor cores: D[a][b] = sum_j z'_ja z'_jb and D[a][36] = sum_j z'_ja
+template <bool BF16>
+__device__ __noinline__ void h1_mixed(Smem& sm, int M, float shift, uint32_t tmem, uint32_t& mph) {
     Hql& h = sm.hql;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int ny = c.ny, nz = ny + 4;
-    const float shift = rintf(c.mean);
+    const int nchunks = (M + kCh - 1) / kCh;
+    __syncthreads();  // the tiles share storage with buffers of the previous phase
+    zero_tiles(h);
+    __syncthreads();
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const int c0 = ch * kCh, n = min(kCh, M - c0);
+        stage_zt<BF16>(sm, c0, n, shift);
+        mma_round(sm, mph, [&]() { mma3(tmem, h.mx.t0, h.mx.t1, h.mx.t0, h.mx.t1, 64, tc::idesc_f16(128, 48, BF16), ch > 0); });
+    }
+    float D[48];
+    if (wid < 2) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 8 * c, &D[8 * c]);
+    }
+    tc::fence_before();
+    __syncthreads();  // the tiles are dead: their storage takes the sums
+    if (wid < 2) {
+        const int a = 32 * wid + lane;
+        if (a < 36) {
+#pragma unroll
+            for (int b = 0; b < 36; ++b) {
+                h.p1.cint[a][b] = 0;
+                h.p1.cfrac[a][b] = D[b];
+            }
+            h.colNi[a] = 0;
+            h.colF[a] = D[36];
+        }
+    }
+    __syncthreads();
+}
+
+// H2 on tensor cores: u_j = L^-1 (y_j - y0) for 64 candidates at a time, d_j = ||u_j||^2
+template <bool BF16>
+__device__ __noinline__ float h2_mixed(Smem& sm, int M, int ny, float shift, uint32_t tmem, uint32_t& mph) {
+    Hql& h = sm.hql;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nchunks = (M + kCh - 1) / kCh;
+    __syncthreads();  // the tiles share storage with buffers of the previous phase
+    zero_tiles(h);
+    __syncthreads();
+    // B = L^-1 (32 rows k x 32 columns l), staged once into t2/t3
+    if (tid < 128) {
+        const int k = tid >> 2, l8 = tid & 3;
+        float v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = h.Linv[k][8 * l8 + t];
+        store8_split<BF16>(h.mx.t2, h.mx.t3, k, 8 * l8, 32, v);
+    }
+    float lmin = INFINITY;
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const int c0 = ch * kCh, n = min(kCh, M - c0);
+        {  // A = E (rows: candidates, columns: context), one task per thread
+            const int j = tid >> 2, l8 = tid & 3;
+            float v[8];
+            const int base = j < n ? h.cand[c0 + j] : 0;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int l = 8 * l8 + t;
+                v[t] = (j < n && l < ny) ? (sm.S[base + h.off[l]] - shift) - h.ys[l] : 0.0f;
+            }
+            store8_split<BF16>(h.mx.t0, h.mx.t1, j, 8 * l8, 32, v);
+        }
+        mma_round(sm, mph, [&]() { mma3(tmem, h.mx.t0, h.mx.t1, h.mx.t2, h.mx.t3, 32, tc::idesc_f16(128, 32, BF16), false); });
+        if (wid < 2) {
+            float u[32];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 8 * c, &u[8 * c]);
+            const int j = 32 * wid + lane;
+            float dd = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) dd = __fmaf_rn(u[k], u[k], dd);
+            if (j < n) {
+                h.d[c0 + j] = dd;
+                lmin = fminf(lmin, dd);
+            }
+        }
+        tc::fence_before();
+        __syncthreads();  // tensor memory read before the next chunk's MMAs
+    }
+    return lmin;
+}
+
+// H3 on tensor cores: D[b][k] = sum_j w_j(b) z'_j[k] with w_j(b) = exp(-(d_j - dmin)/(2 beta_b))
+template <bool BF16>
+__device__ __noinline__ void h3_mixed(Smem& sm, const KParams& P, int M, float shift, float dmin,
+                                         uint32_t tmem, uint32_t& mph) {
+    Hql& h = sm.hql;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nchunks = (M + kCh - 1) / kCh;
+    const int nb = P.nbeta;
+    __syncthreads();  // the tiles share storage with buffers of the previous phase
+    zero_tiles(h);
+    __syncthreads();
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const int c0 = ch * kCh, n = min(kCh, M - c0);
+        stage_zt<BF16>(sm, c0, n, shift);
+        {  // A = W (rows: beta, columns: candidates), one task per thread
+            const int b = tid >> 3, g8 = tid & 7;
+            if (b < nb) {
+                float v[8];
+                const float ib = P.inv2beta[b];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int j = 8 * g8 + t;
+                    v[t] = j < n ? expf(-(h.d[c0 + j] - dmin) * ib) : 0.0f;
+                }
+                store8_split<BF16>(h.mx.t2, h.mx.t3, b, 8 * g8, 64, v);
+            }
+        }
+        mma_round(sm, mph, [&]() { mma3(tmem, h.mx.t2, h.mx.t3, h.mx.t0, h.mx.t1, 64, tc::idesc_f16(128, 48, BF16), ch > 0); });
+    }
+    if (wid == 0) {
+        float D[48];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) tc::tmem_ld8(tmem + 8 * c, &D[8 * c]);
+        if (lane < nb) {
+#pragma unroll
+            for (int k = 0; k < 37; ++k) h.accBd[lane][k] = df_make(D[k]);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+}
+
+// Not inlined: HQL runs for a small share of the patches, and as a function of its own its
+// register demand does not spill the per-step loop of the kernel.
+// The arguments are scalars (the window position, the context mask and size, the context
+// mean), so that the caller's per-step state stays in registers.
+struct HqlOut {
+    float x[4];
+};
+
+template <int MIXED>
+__device__ __noinline__ HqlOut hql_step(Smem& sm, const KParams& P, int wr, int wc,
+                                        unsigned long long ymask, int ny, float mean,
+                                        TraceRec* tr, bool trace, uint32_t& mph) {
+    Hql& h = sm.hql;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nz = ny + 4;
+    const float shift = rintf(mean);
+    StepCtx c;  // the parts of the step context the candidate test needs
+    c.ymask = ymask;
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+        c.rowcfg[r] = (unsigned)((ymask >> (6 * r)) & 63ull) | ((r == 2 || r == 3) ? 12u : 0u);
 
     // context lists (compacted, window raster order)
-    if (tid < 36 && ((c.ymask >> tid) & 1ull)) {
-        const int idx = __popcll(c.ymask & ((1ull << tid) - 1ull));
+    if (tid < 36 && ((ymask >> tid) & 1ull)) {
+        const int idx = __popcll(ymask & ((1ull << tid) - 1ull));
         h.off[idx] = (short)((tid / 6) * kReg + (tid % 6));
-        h.ys[idx] = c.y0w[tid] - shift;
+        h.ys[idx] = sm.S[(wr + tid / 6) * kReg + wc + tid % 6] - shift;
     }
     if (tid >= 64 && tid < 100 && tid - 64 >= ny) {  // zero padding of the lists
         h.off[tid - 64] = 0;
@@ -593,6 +876,11 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
     const int nchunks = (M + kCh - 1) / kCh;
     SK_PHASE(PH_H0);
 
+    if (MIXED == 1) {
+        h1_mixed<true>(sm, M, shift, sm.tmem_base, mph);
+    } else if (MIXED == 2) {
+        h1_mixed<false>(sm, M, shift, sm.tmem_base, mph);
+    } else
     // H1: sums of z' and z' z'^T, z' = z - shift (Eq. (8)).  Thread (a, g) owns row a of the
     // product matrix over the candidates j = g (mod kG1).  Integer parts multiply and
     // accumulate exactly in int32 (|n| <= 255, at most 1849 products: < 2^31); fractional
@@ -779,7 +1067,11 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
     // thread tile: 2 candidates x 4 whitened coordinates
     const int tj = (tid >> 3) * 2, tq = tid & 7;
     float lmin = INFINITY;
-    {
+    if (MIXED == 1) {
+        lmin = h2_mixed<true>(sm, M, ny, shift, sm.tmem_base, mph);
+    } else if (MIXED == 2) {
+        lmin = h2_mixed<false>(sm, M, ny, shift, sm.tmem_base, mph);
+    } else {
         hql_stage(sm, 0, 0, min(kCh, M), shift);
         for (int ch = 0; ch < nchunks; ++ch) {
             const int buf = ch & 1, c0 = ch * kCh, n = min(kCh, M - c0);
@@ -826,7 +1118,11 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
     // j = g (mod kG3): acc[k] = sum_j w_j(b) z'_j[k] for the staged columns (x', y', 1).
     // Subset partial sums merge in double-float.
     const int nb = P.nbeta;
-    {
+    if (MIXED == 1) {
+        h3_mixed<true>(sm, P, M, shift, dmin, sm.tmem_base, mph);
+    } else if (MIXED == 2) {
+        h3_mixed<false>(sm, P, M, shift, dmin, sm.tmem_base, mph);
+    } else {
         const int G3 = kThreads / nb;
         const int b = tid % nb, g = tid / nb;
         const bool act = g < G3;
@@ -1140,10 +1436,11 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
     __syncthreads();
     const float alpha = h.alpha;
     // x0_hat = x~0 + alpha C_XY C_YY^-1 (y0 - y~0), Eq. (13)
+    HqlOut out;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const df32 v = df_add(df_add(df_make(shift), h.xt0d[a]), df_mul_f(h.corr[a], alpha));
-        xhat[a] = df_to_f(v);
+        out.x[a] = df_to_f(v);
     }
     if (trace && tid == 0) {
         tr->beta_idx = (int8_t)bstar;
@@ -1181,12 +1478,15 @@ __device__ __forceinline__ void hql_step(Smem& sm, const KParams& P, const StepC
                            n0u * Mu * (3 * nyu + 2 * (nyu + 5) + 3);
     }
     __syncthreads();
+    return out;
 }
 
 // ------------------------------------------------------------------------------------
 // the persistent kernel
 
-__global__ void __launch_bounds__(kThreads, 2) conceal_kernel(WorkDev W, KParams P) {
+template <int MIXED>
+__global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_constant__ WorkDev W,
+                                                              const __grid_constant__ KParams P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -1195,10 +1495,16 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(WorkDev W, KParams
 
     if (tid == 0) {
         mbar_init(&sm.mbar, 1);
+        tc::mbar_init(&sm.mma_bar, 1);
+        sm.mma_err = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int i = tid; i < kNStats; i += kThreads) sm.st[i] = 0;
+    if (MIXED && wid == 0) tc::tmem_alloc(&sm.tmem_base, 64);  // 128 lanes x 64 FP32 columns
+    tc::fence_before();
     __syncthreads();
+    tc::fence_after();
+    uint32_t mph = 0;
     unsigned phase = 0;
     const int n_entries = W.counters[0];
     if (tid == 0) sm.ph_t = clock64();
@@ -1339,7 +1645,6 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(WorkDev W, KParams
 #pragma unroll
             for (int k = 0; k < 36; ++k) {
                 const float v = sm.S[(c.wr + k / 6) * kReg + c.wc + k % 6];
-                c.y0w[k] = v;
                 if ((c.ymask >> k) & 1ull) {
                     mx = fmaxf(mx, v);
                     mn = fminf(mn, v);
@@ -1370,7 +1675,13 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(WorkDev W, KParams
                 layer = L_BRL;    // Eq. (16)
                 xhat[0] = xhat[1] = xhat[2] = xhat[3] = c.mean;
             } else {
-                const int r = idl_step(sm, P, c, xhat, &ring, &lognu, &evals);
+                const IdlOut io = idl_step(sm, P, c.wr, c.wc, c.ymask, c.ny, c.mean);
+                const int r = io.r;
+                ring = io.ring;
+                lognu = io.lognu;
+                evals = io.evals;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) xhat[a] = io.x[a];
                 SK_PHASE(PH_IDL);
                 if (tid == 0) {
                     sm.st[ST_IDL_EVALS] += evals;
@@ -1386,7 +1697,10 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(WorkDev W, KParams
                 } else {
                     layer = L_HQL;
                     __syncthreads();  // IDL slots -> HQL scratch
-                    hql_step(sm, P, c, xhat, &sm.tr, trace_base != nullptr);
+                    const HqlOut o = hql_step<MIXED>(sm, P, c.wr, c.wc, c.ymask, c.ny, c.mean, &sm.tr,
+                                                     trace_base != nullptr, mph);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) xhat[a] = o.x[a];
                 }
             }
             if (layer == L_EMPTY || layer == L_BRL) SK_PHASE(PH_BRL);
@@ -1446,7 +1760,11 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(WorkDev W, KParams
         if (tid == 0) st_release(&W.done[e], 1u);
         SK_PHASE(PH_PUB);
     }
+    tc::fence_before();
     __syncthreads();
+    tc::fence_after();
+    if (MIXED && wid == 0) tc::tmem_dealloc(sm.tmem_base, 64);
+    if (tid == 0 && sm.mma_err) atomicExch(&W.counters[2], 6);
     for (int i = tid; i < kNStats; i += kThreads)
         if (sm.st[i]) atomicAdd(&W.stats[i], sm.st[i]);
 }
@@ -1592,6 +1910,7 @@ __global__ void __launch_bounds__(kThreads) queue_fill_kernel(WorkDev W) {
 
 namespace sk {
 static_assert(sizeof(Smem) <= 113 * 1024, "two CTAs per SM");
+static_assert(offsetof(Hql, mx) % 16 == 0 && sizeof(Hql::mx) == 4 * 128 * 64 * 2, "tensor-core tiles");
 static_assert(offsetof(Hql, Z) % 16 == 0 && offsetof(Hql, Linv) % 16 == 0 &&
                   offsetof(Hql, ys) % 16 == 0 && offsetof(Smem, hql) % 16 == 0,
               "float4 operands");

@@ -19,16 +19,17 @@ pytestmark = pytest.mark.gpu
 
 FREE_TOL = 0.25      # free-running: bound on |gpu - oracle| before the first decision flip
 PSNR_TOL = 0.01      # dB
+TOL_MIXED = 0.5      # gray levels per pixel, tensor-core contractions (BF16/FP16 split operands)
 
 
-def check(frame, m, p, ctx, free=True):
+def check(frame, m, p, ctx, free=True, tol=None):
     gpu, orc = run_forced(frame, m, p, ctx)
-    rep = compare(frame, m, gpu, orc, p, forced=True)
+    rep = compare(frame, m, gpu, orc, p, forced=True, **({"tol": tol} if tol else {}))
     assert rep["compared"] + rep["flips"] == rep["patches"], rep
     assert rep["flips"] <= max(2, rep["patches"] // 200), rep
     if free:
         g2, o2 = run_pair(frame, m, p, ctx)
-        rep2 = compare(frame, m, g2, o2, p, tol=FREE_TOL)
+        rep2 = compare(frame, m, g2, o2, p, tol=max(FREE_TOL, tol or 0.0))
         s = free_running_summary(frame, m, g2, o2)
         assert abs(s["psnr_gpu"] - s["psnr_oracle"]) <= PSNR_TOL, s
         rep["free"] = {**s, "compared": rep2["compared"], "patches": rep2["patches"],
@@ -143,3 +144,25 @@ def test_argument_errors(gpu_ctx):
     g = torch.randint(0, 255, (32, 32), dtype=torch.uint8, device="cuda")
     out, _, st = gpu_ctx.conceal(g, m, stats=True)
     assert torch.equal(out, g) and st["n_lost_mbs"] == 0
+
+
+# ---------------------------------------------------------------------------------------
+# mixed precision: HQL covariance, whitened distances and beta sums on tcgen05 tensor cores
+
+@pytest.mark.parametrize("precision", [skmmse.MIXED_BF16, skmmse.MIXED_FP16])
+@pytest.mark.parametrize("seed", [1, 2])
+def test_mixed_forced_hql_single_block(gpu_ctx, precision, seed):
+    f, m = synth.workload_single(seed)
+    p = skmmse.params("efficient", t_phi=-1.0, t_nu=1e30, precision=precision)
+    rep, gpu, orc = check(f, m, p, gpu_ctx, tol=TOL_MIXED)
+    assert gpu["stats"]["n_hql"] == 64
+
+
+@pytest.mark.parametrize("precision", [skmmse.MIXED_BF16, skmmse.MIXED_FP16])
+def test_mixed_checkerboard_and_chains(gpu_ctx, precision):
+    f = synth.make_frame(200, 120, 7)
+    m = synth.loss_checkerboard(200, 120)
+    check(f, m, skmmse.params("excellent", precision=precision), gpu_ctx, tol=TOL_MIXED)
+    f = synth.make_frame(256, 160, 8, fine_texture=True)
+    m = synth.loss_runs(256, 160, 3, 0.25)
+    check(f, m, skmmse.params("efficient", precision=precision), gpu_ctx, tol=TOL_MIXED)

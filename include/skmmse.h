@@ -54,7 +54,8 @@ typedef enum {
     SKMMSE_ERR_ALIGN = 3,       /* pointer or pitch alignment not supported */
     SKMMSE_ERR_NOMEM = 4,       /* scratch allocation failed */
     SKMMSE_ERR_CUDA = 5,        /* a CUDA runtime call failed */
-    SKMMSE_ERR_TIMEOUT = 6,     /* a block's dependency wait gave up (device error word) */
+    SKMMSE_ERR_TIMEOUT = 6,     /* a wait on the device gave up, or the work queue found an
+                                   inconsistent block graph (device error word) */
     SKMMSE_ERR_UNSUPPORTED = 7, /* requested precision or flag not built */
     SKMMSE_ERR_TOO_LARGE = 8    /* frame larger than the static scratch of
                                    skmmse_conceal_noalloc (SKMMSE_NOALLOC_MAX_MBS blocks) */
@@ -142,7 +143,8 @@ typedef struct {
     long long alg_flops;        /* algorithmic FP32 operations of the call (per-layer formulas
                                    of the design document; an exp counts as one) */
     long long n_beta;           /* beta grid size of the call */
-    int error;                  /* 0, or SKMMSE_ERR_TIMEOUT */
+    int error;                  /* 0; else the device error word: 6 a wait gave up, 7 the
+                                   work queue met an impossible chain height */
     int pad;
 } skmmse_stats;
 
@@ -180,7 +182,8 @@ skmmse_status skmmse_conceal(skmmse_context* ctx, const uint8_t* d_frame, int wi
                              float* d_out_f32, skmmse_stats* h_stats, void* stream);
 
 /* Conceal n frames of any sizes in one persistent launch (one work queue over all lost
-   blocks of all frames, dependency-ordered).  h_frames is a host array of n descriptors
+   blocks of all frames; a block is claimed once its dependencies are done, the block
+   heading the longest remaining chain first).  h_frames is a host array of n descriptors
    (1 <= n <= 65536). */
 skmmse_status skmmse_conceal_batch(skmmse_context* ctx, const skmmse_frame* h_frames, int n,
                                    const skmmse_params* p, skmmse_stats* h_stats,

@@ -136,8 +136,8 @@ cudaError_t set_kernel_attributes() {
 
 struct BatchLayout {
     long long total_mbs = 0, max_mbs = 1;
-    size_t o_frames = 0, o_tmaps = 0, o_eom = 0, o_ent = 0, o_done = 0, o_vals = 0, o_lev = 0,
-           o_hist = 0, need = 0, stage_bytes = 0;
+    size_t o_frames = 0, o_tmaps = 0, o_eom = 0, o_ent = 0, o_done = 0, o_vals = 0, o_hgt = 0,
+           o_bk = 0, o_rem = 0, o_slots = 0, need = 0, stage_bytes = 0;
 };
 
 skmmse_status plan_batch(const skmmse_frame* frames, int n, const skmmse_params* p, BatchLayout* L) {
@@ -160,8 +160,10 @@ skmmse_status plan_batch(const skmmse_frame* frames, int n, const skmmse_params*
     L->o_ent = off; off = align_up(off + sizeof(int4) * L->total_mbs, 128);
     L->o_done = off; off = align_up(off + sizeof(unsigned) * L->total_mbs, 128);
     L->o_vals = off; off = align_up(off + sizeof(float) * 256 * L->total_mbs, 128);
-    L->o_lev = off; off = align_up(off + sizeof(int) * L->total_mbs, 128);
-    L->o_hist = off; off = align_up(off + sizeof(int) * 2 * L->max_mbs, 128);  // hist + cursor
+    L->o_hgt = off; off = align_up(off + sizeof(int) * L->total_mbs, 128);
+    L->o_bk = off; off = align_up(off + sizeof(int) * 4 * L->max_mbs, 128);  // off, cnt, head, tail
+    L->o_rem = off; off = align_up(off + sizeof(int) * L->total_mbs, 128);
+    L->o_slots = off; off = align_up(off + sizeof(int) * L->total_mbs, 128);
     L->need = off;
     return SKMMSE_OK;
 }
@@ -219,7 +221,8 @@ skmmse_status enqueue_batch(const skmmse_frame* frames, int n, const BatchLayout
     }
     SK_CHECK(cudaMemsetAsync(counters, 0, 4 * sizeof(int), stream));
     SK_CHECK(cudaMemsetAsync(stats, 0, sk::kNStats * sizeof(unsigned long long), stream));
-    SK_CHECK(cudaMemsetAsync(arena + L.o_hist, 0, sizeof(int) * 2 * L.max_mbs, stream));
+    SK_CHECK(cudaMemsetAsync(arena + L.o_bk, 0, sizeof(int) * 4 * L.max_mbs, stream));
+    SK_CHECK(cudaMemsetAsync(arena + L.o_slots, 0xFF, sizeof(int) * L.total_mbs, stream));
     WorkDev w;
     w.frames = reinterpret_cast<const FrameDev*>(arena + L.o_frames);
     w.tmaps = reinterpret_cast<const CUtensorMap*>(arena + L.o_tmaps);
@@ -230,13 +233,17 @@ skmmse_status enqueue_batch(const skmmse_frame* frames, int n, const BatchLayout
     w.done = reinterpret_cast<unsigned*>(arena + L.o_done);
     w.vals = reinterpret_cast<float*>(arena + L.o_vals);
     w.stats = stats;
-    w.level_of_mb = reinterpret_cast<int*>(arena + L.o_lev);
-    w.lvl_hist = reinterpret_cast<int*>(arena + L.o_hist);
-    w.lvl_cursor = w.lvl_hist + L.max_mbs;
-    w.nlev = (int)L.max_mbs;
-    sk::queue_levels_kernel<<<n, sk::kThreads, 0, stream>>>(w, kp.concealed_is_support);
+    w.height_of_mb = reinterpret_cast<int*>(arena + L.o_hgt);
+    w.bk_off = reinterpret_cast<int*>(arena + L.o_bk);
+    w.bk_cnt = w.bk_off + L.max_mbs;
+    w.bk_head = w.bk_cnt + L.max_mbs;
+    w.bk_tail = w.bk_head + L.max_mbs;
+    w.rem = reinterpret_cast<int*>(arena + L.o_rem);
+    w.slots = reinterpret_cast<int*>(arena + L.o_slots);
+    w.nbk = (int)L.max_mbs;
+    sk::queue_heights_kernel<<<n, sk::kThreads, 0, stream>>>(w, kp.concealed_is_support);
     sk::queue_offsets_kernel<<<1, sk::kThreads, 0, stream>>>(w);
-    sk::queue_fill_kernel<<<n, sk::kThreads, 0, stream>>>(w);
+    sk::queue_fill_kernel<<<n, sk::kThreads, 0, stream>>>(w, kp.concealed_is_support);
     SK_CHECK(cudaGetLastError());
     if (grid > L.total_mbs) grid = L.total_mbs;
     if (grid < 1) grid = 1;
@@ -264,7 +271,8 @@ skmmse_status read_stats_from(const unsigned long long* d_stats, const int* d_co
 // Scratch for skmmse_conceal_noalloc(): one file-scope device array, sized for frames of up
 // to SKMMSE_NOALLOC_MAX_MBS blocks.  Every GPU that loads the library holds it until the
 // process exits.  Layout (byte offsets, each 256-aligned): frame descriptor, tensor map,
-// counters + stats, entry_of_mb, entries, done flags, per-block values.
+// counters + stats, entry_of_mb, entries, done flags, per-block values, heights, buckets,
+// dependency counts, ready slots.
 constexpr size_t kNaMax = SKMMSE_NOALLOC_MAX_MBS;
 constexpr size_t kNaFrame = 0;
 constexpr size_t kNaTmap = 256;
@@ -274,9 +282,11 @@ constexpr size_t kNaEom = align_up(kNaStats + sizeof(unsigned long long) * sk::k
 constexpr size_t kNaEnt = align_up(kNaEom + sizeof(int) * kNaMax, 256);
 constexpr size_t kNaDone = align_up(kNaEnt + sizeof(int4) * kNaMax, 256);
 constexpr size_t kNaVals = align_up(kNaDone + sizeof(unsigned) * kNaMax, 256);
-constexpr size_t kNaLev = align_up(kNaVals + sizeof(float) * 256 * kNaMax, 256);
-constexpr size_t kNaHist = align_up(kNaLev + sizeof(int) * kNaMax, 256);  // hist + cursor
-constexpr size_t kNaBytes = align_up(kNaHist + sizeof(int) * 2 * kNaMax, 256);
+constexpr size_t kNaHgt = align_up(kNaVals + sizeof(float) * 256 * kNaMax, 256);
+constexpr size_t kNaBk = align_up(kNaHgt + sizeof(int) * kNaMax, 256);  // off, cnt, head, tail
+constexpr size_t kNaRem = align_up(kNaBk + sizeof(int) * 4 * kNaMax, 256);
+constexpr size_t kNaSlots = align_up(kNaRem + sizeof(int) * kNaMax, 256);
+constexpr size_t kNaBytes = align_up(kNaSlots + sizeof(int) * kNaMax, 256);
 static_assert(sizeof(FrameDev) <= 256 && sizeof(CUtensorMap) <= 256, "scratch header");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
@@ -290,10 +300,12 @@ __global__ void noalloc_setup_kernel(FrameDev fd, CUtensorMap tm, unsigned char*
     }
     int* counters = reinterpret_cast<int*>(scratch + kNaCounters);
     unsigned long long* stats = reinterpret_cast<unsigned long long*>(scratch + kNaStats);
-    int* hist = reinterpret_cast<int*>(scratch + kNaHist);
+    int* bk = reinterpret_cast<int*>(scratch + kNaBk);
+    int* slots = reinterpret_cast<int*>(scratch + kNaSlots);
     if (threadIdx.x < 4) counters[threadIdx.x] = 0;
     for (int i = threadIdx.x; i < sk::kNStats; i += blockDim.x) stats[i] = 0ull;
-    for (int i = threadIdx.x; i < 2 * (int)kNaMax; i += blockDim.x) hist[i] = 0;
+    for (int i = threadIdx.x; i < 4 * (int)kNaMax; i += blockDim.x) bk[i] = 0;
+    for (int i = threadIdx.x; i < (int)kNaMax; i += blockDim.x) slots[i] = -1;
 }
 
 struct NoAllocDevice {
@@ -690,14 +702,18 @@ skmmse_status skmmse_conceal_noalloc(const uint8_t* d_frame, int width, int heig
     w.done = reinterpret_cast<unsigned*>(sc + kNaDone);
     w.vals = reinterpret_cast<float*>(sc + kNaVals);
     w.stats = reinterpret_cast<unsigned long long*>(sc + kNaStats);
-    w.level_of_mb = reinterpret_cast<int*>(sc + kNaLev);
-    w.lvl_hist = reinterpret_cast<int*>(sc + kNaHist);
-    w.lvl_cursor = w.lvl_hist + kNaMax;
-    w.nlev = (int)(mbw * mbh);
+    w.height_of_mb = reinterpret_cast<int*>(sc + kNaHgt);
+    w.bk_off = reinterpret_cast<int*>(sc + kNaBk);
+    w.bk_cnt = w.bk_off + kNaMax;
+    w.bk_head = w.bk_cnt + kNaMax;
+    w.bk_tail = w.bk_head + kNaMax;
+    w.rem = reinterpret_cast<int*>(sc + kNaRem);
+    w.slots = reinterpret_cast<int*>(sc + kNaSlots);
+    w.nbk = (int)(mbw * mbh);
     const KParams kp = make_kparams(p);
-    sk::queue_levels_kernel<<<1, sk::kThreads, 0, stream>>>(w, kp.concealed_is_support);
+    sk::queue_heights_kernel<<<1, sk::kThreads, 0, stream>>>(w, kp.concealed_is_support);
     sk::queue_offsets_kernel<<<1, sk::kThreads, 0, stream>>>(w);
-    sk::queue_fill_kernel<<<1, sk::kThreads, 0, stream>>>(w);
+    sk::queue_fill_kernel<<<1, sk::kThreads, 0, stream>>>(w, kp.concealed_is_support);
     SK_CHECK(cudaGetLastError());
     long long grid = (long long)nd->sm_count * nd->blocks_per_sm;
     if (grid > mbw * mbh) grid = mbw * mbh;

@@ -113,15 +113,19 @@ struct WorkDev {
     const CUtensorMap* tmaps;
     int nframes;
     int* entry_of_mb;         // per block of all frames: queue entry or -1
-    int4* entries;            // (frame, block index, rank among the frame's lost blocks, level)
-    int* counters;            // [0] entries, [1] queue head, [2] error word
+    int4* entries;            // (frame, block index, rank among the frame's lost blocks, bucket)
+    int* counters;            // [0] entries, [1] claimed, [2] error word, [3] first live bucket
     unsigned* done;           // per entry: 0 pending, 1 done, 2 done with error
     float* vals;              // per entry: 256 unrounded values of the block
     unsigned long long* stats;
-    int* level_of_mb;         // per block of all frames: dependency level (-1 received)
-    int* lvl_hist;            // per level: number of lost blocks, then the level's first entry
-    int* lvl_cursor;          // per level: entries handed out so far
-    int nlev;                 // levels allocated (>= blocks of the largest frame)
+    int* height_of_mb;        // per block of all frames: longest chain of dependants (-1 received)
+    int* bk_off;              // per bucket: number of entries, then the bucket's first entry
+    int* bk_cnt;              // per bucket: entries handed out while filling (= its size after)
+    int* bk_head;             // per bucket: ready entries claimed
+    int* bk_tail;             // per bucket: ready entries published
+    int* rem;                 // per entry: dependencies not yet done
+    int* slots;               // per entry position: the ready entries of each bucket, -1 until published
+    int nbk;                  // buckets allocated (>= blocks of the largest frame)
 };
 
 struct TraceRec {             // layout of skmmse_trace_rec
@@ -240,6 +244,22 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 
 __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire_i(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_i(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_i(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
@@ -1484,6 +1504,92 @@ __device__ __noinline__ HqlOut hql_step(Smem& sm, const KParams& P, int wr, int 
 // ------------------------------------------------------------------------------------
 // the persistent kernel
 
+// ------------------------------------------------------------------------------------
+// Ready queue (see the work-queue notes below the kernel).  Called by warp 0 of a CTA;
+// returns the claimed entry, -1 when every entry is claimed, -2 on a timeout (error word
+// set).  The bound counts idle rounds without progress of the whole call.
+__device__ __noinline__ int claim_ready(const WorkDev& W, int n_entries) {
+    const int lane = threadIdx.x & 31;
+    unsigned idle = 0;
+    int seen = -1;
+    for (;;) {
+        const int claimed = ld_relaxed_i(&W.counters[1]);
+        if (claimed >= n_entries) return -1;
+        if (claimed != seen) {
+            seen = claimed;
+            idle = 0;
+        }
+        const int k0 = ld_relaxed_i(&W.counters[3]);
+        bool lost_race = false;
+        for (int kb = k0; kb < W.nbk; kb += 32) {
+            const int k = kb + lane;
+            int hd = 0, tl = 0, cnt = 0;
+            if (k < W.nbk) {
+                hd = ld_relaxed_i(&W.bk_head[k]);
+                tl = ld_relaxed_i(&W.bk_tail[k]);
+                cnt = W.bk_cnt[k];
+            }
+            const unsigned ready = __ballot_sync(0xffffffffu, k < W.nbk && hd < tl);
+            if (kb == k0) {  // buckets fully claimed at the front never refill: move the start
+                const unsigned drained = __ballot_sync(0xffffffffu, k >= W.nbk || hd >= cnt);
+                const int adv = drained == 0xffffffffu ? 32 : __ffs(~drained) - 1;
+                if (adv > 0 && lane == 0) atomicMax(&W.counters[3], kb + adv);
+            }
+            if (ready) {
+                const int src = __ffs(ready) - 1;
+                int pos = -1;
+                if (lane == src && atomicCAS(&W.bk_head[k], hd, hd + 1) == hd) pos = W.bk_off[k] + hd;
+                pos = __shfl_sync(0xffffffffu, pos, src);
+                if (pos < 0) {
+                    lost_race = true;
+                    break;
+                }
+                int e = -1;
+                if (lane == 0) {
+                    atomicAdd(&W.counters[1], 1);
+                    // the publisher advances the tail just before it writes the slot
+                    unsigned it = 0;
+                    while ((e = ld_acquire_i(&W.slots[pos])) < 0) {
+                        __nanosleep(32);
+                        if (++it > (1u << 24)) {
+                            atomicExch(&W.counters[2], 6);
+                            break;
+                        }
+                    }
+                }
+                e = __shfl_sync(0xffffffffu, e, 0);
+                return e < 0 ? -2 : e;
+            }
+        }
+        if (lost_race) continue;
+        __nanosleep(256);
+        if (++idle > (1u << 25)) {
+            if (lane == 0) atomicExch(&W.counters[2], 6);
+            return -2;
+        }
+    }
+}
+
+// entry e (block mb of frame F) is done: count it off at each dependant and publish the
+// dependants that became ready.  One thread.
+__device__ __noinline__ void release_dependants(const WorkDev& W, const FrameDev& F, int mb) {
+    const int y = mb / F.mbw, x = mb - (mb / F.mbw) * F.mbw;
+    __threadfence();  // the done flag before the counts
+    const int dys[4] = {0, 1, 1, 1}, dxs[4] = {1, -1, 0, 1};
+    for (int t = 0; t < 4; ++t) {
+        const int yy = y + dys[t], xx = x + dxs[t];
+        if (yy >= F.mbh || xx < 0 || xx >= F.mbw) continue;
+        const int qe = W.entry_of_mb[F.mb_base + yy * F.mbw + xx];
+        if (qe < 0) continue;
+        if (atomicSub(&W.rem[qe], 1) == 1) {
+            __threadfence();
+            const int key = W.entries[qe].w;
+            const int k = atomicAdd(&W.bk_tail[key], 1);
+            st_release_i(&W.slots[W.bk_off[key] + k], qe);
+        }
+    }
+}
+
 template <int MIXED>
 __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_constant__ WorkDev W,
                                                               const __grid_constant__ KParams P) {
@@ -1510,10 +1616,13 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
     if (tid == 0) sm.ph_t = clock64();
 
     for (;;) {
-        if (tid == 0) sm.entry = atomicAdd(&W.counters[1], 1);
+        if (wid == 0) {
+            const int got = claim_ready(W, n_entries);
+            if (lane == 0) sm.entry = got;
+        }
         __syncthreads();
         const int e = sm.entry;
-        if (e >= n_entries) break;
+        if (e < 0) break;
         const int4 ent = W.entries[e];
         const FrameDev& F = W.frames[ent.x];
         const int mb = ent.y, mby = mb / F.mbw, mbx = mb - (mb / F.mbw) * F.mbw;
@@ -1757,7 +1866,10 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
         }
         __threadfence();
         __syncthreads();
-        if (tid == 0) st_release(&W.done[e], 1u);
+        if (tid == 0) {
+            st_release(&W.done[e], 1u);
+            if (P.concealed_is_support) release_dependants(W, F, mb);
+        }
         SK_PHASE(PH_PUB);
     }
     tc::fence_before();
@@ -1770,12 +1882,14 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
 }
 
 // ------------------------------------------------------------------------------------
-// Queue construction.  The queue lists every lost block of every frame ordered by its
-// dependency level: level 0 for a block none of whose earlier-in-raster lost neighbours
-// (left, top-left, top, top-right) is support, else 1 + the largest level among them.
-// Every dependency of an entry therefore sits at a lower level, earlier in the queue, so
-// a CTA only waits for blocks that running CTAs already hold (no deadlock), and blocks of
-// one level, independent of each other, run side by side.
+// Work queue.  A lost block depends on its lost neighbours earlier in raster order (left,
+// top-left, top, top-right) when concealed pixels are support.  The blocks of a call are
+// grouped into buckets by their height, the length of the longest chain of blocks that
+// depend on them (0 for a block nothing waits for); bucket key = nbk - 1 - height, so low
+// keys hold the blocks that head the longest chains.  A block becomes ready when its last
+// dependency is done and is then published in its bucket; a free CTA claims a ready block
+// of the lowest live key (highest height first: list scheduling by critical path).  A CTA
+// only ever claims ready blocks, so no CTA holds an SM while it waits for a dependency.
 
 struct SegFV {
     int f;  // a segment starts inside the combined range
@@ -1809,50 +1923,55 @@ __device__ __forceinline__ SegFV block_seg_scan(SegFV x, SegFV* sh /*[kWarps]*/)
 
 constexpr int kLevelNeg = -(1 << 29);
 
-// one CTA per frame: dependency level of every lost block, row by row.  Within a row a run
-// of lost blocks chains through the left neighbour, so level[x] = x + max over the run up
-// to x of (up[k] - k), up[k] = max(0, 1 + level of the lost blocks above k): a segmented
-// max-scan.  Also counts the lost blocks of each level and of the whole call.
-__global__ void __launch_bounds__(kThreads) queue_levels_kernel(WorkDev W, int support) {
+// one CTA per frame: height of every lost block, rows from the bottom up.  The dependants
+// of (y, x) are the lost blocks (y, x+1) and (y+1, x-1 .. x+1).  Within a row a run of lost
+// blocks chains through the right neighbour, so with the mirrored column x' = mbw-1-x,
+// height[x'] = x' + max over the run up to x' of (down[k'] - k'), down = max(0, 1 + height
+// of the lost blocks below): a segmented max-scan.  Also counts the blocks of each bucket.
+__global__ void __launch_bounds__(kThreads) queue_heights_kernel(WorkDev W, int support) {
     __shared__ SegFV sh[kWarps];
     __shared__ int carry_s;
     __shared__ int cnt_s;
     const int f = blockIdx.x, tid = threadIdx.x;
     const FrameDev& F = W.frames[f];
-    int* lev = W.level_of_mb + F.mb_base;
+    int* hgt = W.height_of_mb + F.mb_base;
     if (tid == 0) cnt_s = 0;
     int cnt = 0;
-    for (int y = 0; y < F.mbh; ++y) {
+    for (int y = F.mbh - 1; y >= 0; --y) {
         if (tid == 0) carry_s = kLevelNeg;
         __syncthreads();
         for (int x0 = 0; x0 < F.mbw; x0 += kThreads) {
-            const int x = x0 + tid;
-            const bool lost = x < F.mbw && F.lost[y * F.mbw + x] != 0;
-            int up = 0;
-            if (lost && support && y > 0) {
+            const int xm = x0 + tid, x = F.mbw - 1 - xm;
+            const bool in = xm < F.mbw;
+            const bool lost = in && F.lost[y * F.mbw + x] != 0;
+            int down = 0;
+            if (lost && support && y + 1 < F.mbh) {
                 for (int dx = -1; dx <= 1; ++dx) {
                     const int xx = x + dx;
-                    if (xx >= 0 && xx < F.mbw && F.lost[(y - 1) * F.mbw + xx])
-                        up = max(up, lev[(y - 1) * F.mbw + xx] + 1);
+                    if (xx >= 0 && xx < F.mbw && F.lost[(y + 1) * F.mbw + xx])
+                        down = max(down, hgt[(y + 1) * F.mbw + xx] + 1);
                 }
             }
-            const bool left_lost = x > 0 && x - 1 < F.mbw && F.lost[y * F.mbw + x - 1] != 0;
+            const bool right_lost = in && x + 1 < F.mbw && F.lost[y * F.mbw + x + 1] != 0;
             SegFV e;
-            e.f = (!lost || !left_lost || !support) ? 1 : 0;
-            e.v = lost ? up - x : kLevelNeg;
+            e.f = (!lost || !right_lost || !support) ? 1 : 0;
+            e.v = lost ? down - xm : kLevelNeg;
             // a run continuing from the previous chunk starts without a head in this chunk
-            if (tid == 0 && x0 > 0 && lost && left_lost && support) e.f = 0;
+            if (tid == 0 && x0 > 0 && lost && right_lost && support) e.f = 0;
             SegFV r = block_seg_scan(e, sh);
             const int carry = carry_s;
             if (!r.f) r.v = max(r.v, carry);
-            int level = -1;
             if (lost) {
-                level = support ? x + r.v : 0;
-                lev[y * F.mbw + x] = level;
-                atomicAdd(&W.lvl_hist[level], 1);
+                int h = support ? xm + r.v : 0;
+                if (h < 0 || h >= W.nbk) {  // cannot happen (a chain has at most nbk blocks)
+                    atomicExch(&W.counters[2], 7);
+                    h = min(max(h, 0), W.nbk - 1);
+                }
+                hgt[y * F.mbw + x] = h;
+                atomicAdd(&W.bk_off[W.nbk - 1 - h], 1);
                 ++cnt;
-            } else if (x < F.mbw) {
-                lev[y * F.mbw + x] = -1;
+            } else if (in) {
+                hgt[y * F.mbw + x] = -1;
             }
             __syncthreads();
             if (tid == kThreads - 1) carry_s = (lost && support) ? r.v : kLevelNeg;
@@ -1864,23 +1983,31 @@ __global__ void __launch_bounds__(kThreads) queue_levels_kernel(WorkDev W, int s
     if (tid == 0) atomicAdd(&W.counters[0], cnt_s);
 }
 
-// one CTA: exclusive scan of the level histogram into first-entry offsets
+// one CTA: exclusive scan of the bucket sizes into first-entry offsets; the first non-empty
+// bucket starts the claim scan
 __global__ void __launch_bounds__(kThreads) queue_offsets_kernel(WorkDev W) {
     __shared__ int scan[kWarps + 1];
+    __shared__ int first_s;
+    if (threadIdx.x == 0) first_s = W.nbk;
+    __syncthreads();
     int run = 0;
-    for (int l0 = 0; l0 < W.nlev; l0 += kThreads) {
+    for (int l0 = 0; l0 < W.nbk; l0 += kThreads) {
         const int l = l0 + threadIdx.x;
-        const int v = l < W.nlev ? W.lvl_hist[l] : 0;
+        const int v = l < W.nbk ? W.bk_off[l] : 0;
+        if (v > 0) atomicMin(&first_s, l);
         int tot;
         const int ex = block_exscan(v, scan, &tot) + run;
-        if (l < W.nlev) W.lvl_hist[l] = ex;
+        if (l < W.nbk) W.bk_off[l] = ex;
         run += tot;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) W.counters[3] = first_s;
 }
 
-// one CTA per frame: every lost block takes the next entry of its level; the rank among
-// the frame's lost blocks in raster order indexes its trace records
-__global__ void __launch_bounds__(kThreads) queue_fill_kernel(WorkDev W) {
+// one CTA per frame: every lost block takes the next entry of its bucket and counts its
+// dependencies; blocks without any are published as ready.  The rank among the frame's
+// lost blocks in raster order indexes its trace records.
+__global__ void __launch_bounds__(kThreads) queue_fill_kernel(WorkDev W, int support) {
     __shared__ int scan[kWarps + 1];
     const int f = blockIdx.x;
     const FrameDev& F = W.frames[f];
@@ -1893,11 +2020,27 @@ __global__ void __launch_bounds__(kThreads) queue_fill_kernel(WorkDev W) {
         const int rank = block_exscan(lost, scan, &tot) + run;
         if (i < nmb) {
             if (lost) {
-                const int level = W.level_of_mb[F.mb_base + i];
-                const int e = W.lvl_hist[level] + atomicAdd(&W.lvl_cursor[level], 1);
+                const int key = W.nbk - 1 - W.height_of_mb[F.mb_base + i];
+                const int e = W.bk_off[key] + atomicAdd(&W.bk_cnt[key], 1);
                 W.entry_of_mb[F.mb_base + i] = e;
-                W.entries[e] = make_int4(f, i, rank, level);
+                W.entries[e] = make_int4(f, i, rank, key);
                 W.done[e] = 0u;
+                int ndep = 0;
+                if (support) {
+                    const int y = i / F.mbw, x = i - y * F.mbw;
+                    if (x > 0 && F.lost[i - 1]) ++ndep;
+                    if (y > 0) {
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int xx = x + dx;
+                            if (xx >= 0 && xx < F.mbw && F.lost[i - F.mbw + dx]) ++ndep;
+                        }
+                    }
+                }
+                W.rem[e] = ndep;
+                if (ndep == 0) {
+                    const int k = atomicAdd(&W.bk_tail[key], 1);
+                    W.slots[W.bk_off[key] + k] = e;
+                }
             } else {
                 W.entry_of_mb[F.mb_base + i] = -1;
             }

@@ -6,13 +6,18 @@ Workload (one "step"): the batch of 64 seeded synthetic frames of mixed sizes (2
 blocks, half runs of 4-20 blocks), concealed by one skmmse_conceal_batch call: one
 persistent work-queue launch over every lost 16x16 block of the 64 frames.
 
-Prints one JSON line: concealed 16x16 blocks per second (value, inputs resident in HBM,
-device time by CUDA events on the launching stream, L2 flushed between steps), the same
-metric end to end through the C ABI with host buffers (e2e), the roofline of the
-concealment kernel, the CPU baseline (the FP64 oracle on a bounded sample, host cores)
-and SM clocks sampled during the timed region.
+The timed step runs at --precision (default bf16: the HQL contractions on tensor cores,
+everything else FP32).  Prints one JSON line: concealed 16x16 blocks per second (value,
+inputs resident in HBM, device time by CUDA events on the launching stream, L2 flushed
+between steps), the same metric end to end through the C ABI with host buffers (e2e),
+the roofline of the concealment kernel, SM clocks sampled during the timed region, and:
+  compare     the same batch in FP32, the FP32 single-frame form (one call per frame),
+              1080p frames/s in both precisions, PSNR delta of the output against FP32;
+  cpu_baseline the FP64 oracle on a bounded sample of the batch on the host cores;
+  vs_oracle   PSNR delta and largest pixel difference against the oracle on that sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision bf16|fp16|fp32] [--workload ...] [--no-compare]
 Under torchrun (N > 1) every rank conceals its own batch (replicas, weak scaling).
 """
 from __future__ import annotations
@@ -31,12 +36,14 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "concealed 16x16 MBs/s"
+METRIC = "concealed 16x16 MBs/s and 1080p frames/s on 1 GB300, mixed vs FP32, at \u22640.01 dB PSNR delta"
 UNIT = "MB/s"
 WORKLOAD = "batch64_mixed_24x352x288_24x1280x720_16x1920x1080_loss5-30pct"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
+DTYPES = {"fp32": "f32", "bf16": "bf16+f32", "fp16": "f16+f32"}
 
 
 def parse():
@@ -53,6 +60,10 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="serving stream length (20000 = the full 600 frames/s stream of ~33 s)")
     ap.add_argument("--autotune", action="store_true", help="pick CTAs per SM before timing")
+    ap.add_argument("--precision", choices=list(PRECISIONS), default="bf16",
+                    help="bf16 / fp16: HQL contractions on tensor cores (mixed); fp32: CUDA cores only")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the FP32 / single-frame / 1080p comparison legs")
     return ap.parse_args()
 
 
@@ -165,16 +176,18 @@ def cpu_baseline(frames, masks, profile: str, budget_s: float = 25.0):
                 picked.append((f, m))
                 break
     mbs = 0
+    outs = []
     t0 = time.perf_counter()
     for f, m in picked:
-        oracle.conceal(f, m, p, threads=cores)
+        outs.append(oracle.conceal(f, m, p, threads=cores)["out"])
         mbs += int(m.sum())
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": mbs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(picked)} frames of the batch (352x288, 1280x720, 1920x1080 at the "
+    line = {"value": mbs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(outs)} frames of the batch (352x288, 1280x720, 1920x1080 at the "
                       f"batch's seeds), {mbs} lost blocks, {dt:.1f} s, all host cores"}
+    return line, [(f, m, o) for (f, m), o in zip(picked, outs)]
 
 
 def run_reference(args):
@@ -215,6 +228,67 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _time_calls(fn, reps: int, flush, stream) -> float:
+    """Median milliseconds of fn() over reps calls, L2 flushed before each, CUDA events on
+    the launching stream."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def compare_legs(ctx, skmmse, args, frames, masks, fd, md, od, p_main, ms_main, flush, stream):
+    """The other sides of "mixed vs FP32": the batch in FP32, the FP32 single-frame form
+    (one call per frame), 1080p frames/s, and the PSNR of the mixed output against FP32."""
+    import torch
+    from paper_2205_11226_gb300 import synth
+    n_lost = sum(int(m.sum()) for m in masks)
+    p32 = skmmse.params(args.profile, precision=0)
+    o32 = [torch.empty_like(f) for f in fd]
+    ms_b32 = _time_calls(lambda: ctx.conceal_batch(fd, md, p32, outs=o32, stream=stream), 3, flush, stream)
+
+    def single_frames():
+        for f, m, o in zip(fd, md, o32):
+            ctx.conceal(f, m, p32, out=o, stream=stream)
+    ms_s32 = _time_calls(single_frames, 2, flush, stream)
+    # PSNR over the lost pixels against the undamaged frame, main precision vs FP32
+    ctx.conceal_batch(fd, md, p_main, outs=od, stream=stream)
+    ctx.conceal_batch(fd, md, p32, outs=o32, stream=stream)
+    torch.cuda.synchronize()
+    dpsnr, dmax = 0.0, 0
+    for i in range(len(frames)):
+        lm = synth.lost_pixel_mask(masks[i], frames[i].shape[1], frames[i].shape[0])
+        a, b = od[i].cpu().numpy(), o32[i].cpu().numpy()
+        dpsnr = max(dpsnr, abs(synth.psnr(a, frames[i], lm) - synth.psnr(b, frames[i], lm)))
+        dmax = max(dmax, int(np.abs(a.astype(np.int32) - b.astype(np.int32)).max()))
+    # one 1920x1080 frame (runs of 4-20 lost blocks to 20 %, fine texture), one call per frame
+    f1, m1 = synth.workload_slice_1080p(args.seed)
+    f1d, m1d = torch.from_numpy(f1).cuda(), torch.from_numpy(m1).cuda()
+    o1 = torch.empty_like(f1d)
+    fps = {}
+    for name, pp in ((args.precision, p_main), ("fp32", p32)):
+        ms1 = _time_calls(lambda: ctx.conceal(f1d, m1d, pp, out=o1, stream=stream), 5, flush, stream)
+        fps[name] = 1e3 / ms1
+    return {"fp32_batched_mbs_per_s": n_lost / (ms_b32 * 1e-3),
+            "fp32_single_frame_mbs_per_s": n_lost / (ms_s32 * 1e-3),
+            "speedup_vs_fp32_single_frame": ms_s32 / ms_main,
+            "speedup_vs_fp32_batched": ms_b32 / ms_main,
+            "frames_1080p_per_s": fps,
+            "frames_1080p_workload": "1920x1080, runs of 4-20 lost blocks to 20 %, fine texture, "
+                                     f"{int(m1.sum())} lost blocks, one call per frame",
+            "psnr_delta_db_vs_fp32_max_frame": dpsnr,
+            "max_abs_diff_gray_vs_fp32_uint8": dmax}
+
+
 def run_ours(args):
     import torch
     from paper_2205_11226_gb300 import build as skbuild
@@ -229,7 +303,7 @@ def run_ours(args):
     skbuild.build()
     from paper_2205_11226_gb300 import skmmse
     frames, masks = build_workload(rank_seed(args.seed, rank), args.workload)
-    p = skmmse.params(args.profile)
+    p = skmmse.params(args.profile, precision=PRECISIONS[args.precision])
     ctx = skmmse.Context()
     stream = torch.cuda.current_stream()
     fd = [torch.from_numpy(f).cuda() for f in frames]
@@ -297,10 +371,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     e2e_ms = float(sum(a.elapsed_time(b) for a, b in e2e_ev))
-    # outputs of the end-to-end leg are the concealed frames
-    assert all(np.array_equal(ho[i].numpy()[~np.kron(masks[i].astype(bool), np.ones((16, 16), bool))[:frames[i].shape[0], :frames[i].shape[1]]],
-                              frames[i][~np.kron(masks[i].astype(bool), np.ones((16, 16), bool))[:frames[i].shape[0], :frames[i].shape[1]]])
-               for i in range(0, len(frames), 16))
+    # outputs of the end-to-end leg are the concealed frames: received pixels unchanged
+    for i in range(0, len(frames), 16):
+        keep = ~synth_lost_mask(masks[i], frames[i].shape)
+        assert np.array_equal(ho[i].numpy()[keep], frames[i][keep])
 
     total_ms, e2e_ms, units = reduce_over_ranks(dist, total_ms, e2e_ms, n_lost, "cuda")
     value = units * args.steps / (total_ms * 1e-3)
@@ -315,29 +389,58 @@ def run_ours(args):
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived)",
                 "alg_flops_per_step": flops}
     if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
             "data": "synthetic (seeded generator standing in for Kodak/ClassB/ClassC; no dataset)",
             "config": {"workload": WORKLOADS[args.workload], "frames": len(frames), "lost_mbs_per_step": n_lost,
-                       "profile": args.profile, "precision": "fp32",
+                       "profile": args.profile, "precision": args.precision,
                        "l2": "flushed between steps (256 MiB write)",
                        "ctas_per_sm": tuned["ctas_per_sm"] if tuned else "occupancy max",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": 4 * args.steps,
             "roofline": roofline,
             "layers": {k: st[k] for k in ("n_patches", "n_brl", "n_idl", "n_hql", "n_brl_nocand")},
             "wall_s_timed": t_wall,
             "clocks": clocks}
+    if ws == 1 and not args.no_compare and args.workload == "batch":
+        line["compare"] = compare_legs(ctx, skmmse, args, frames, masks, fd, md, od, p, mean_ms, flush,
+                                       stream)
     if ws == 1 and not args.no_cpu_baseline and args.workload == "batch":
-        line["cpu_baseline"] = cpu_baseline(frames, masks, args.profile)
+        cb, sample = cpu_baseline(frames, masks, args.profile)
+        line["cpu_baseline"] = cb
+        line["vs_oracle"] = oracle_agreement(frames, masks, od, sample)
     print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def synth_lost_mask(mb_lost, shape):
+    from paper_2205_11226_gb300 import synth
+    return synth.lost_pixel_mask(mb_lost, shape[1], shape[0])
+
+
+def oracle_agreement(frames, masks, od, sample):
+    """Main-precision output against the FP64 oracle on the CPU sample frames: PSNR delta
+    over the lost pixels and the largest per-pixel difference (both rounded to 8 bits)."""
+    from paper_2205_11226_gb300 import synth
+    res = {"frames": len(sample), "psnr_delta_db_max": 0.0, "max_abs_diff_gray_uint8": 0}
+    for f, m, o in sample:
+        i = next(k for k in range(len(frames)) if frames[k] is f)
+        lm = synth_lost_mask(m, f.shape)
+        ours = od[i].cpu().numpy()
+        ref = np.clip(np.rint(o), 0, 255).astype(np.uint8)
+        res["psnr_delta_db_max"] = max(res["psnr_delta_db_max"],
+                                       abs(synth.psnr(ours, f, lm) - synth.psnr(ref, f, lm)))
+        res["max_abs_diff_gray_uint8"] = max(res["max_abs_diff_gray_uint8"],
+                                             int(np.abs(ours.astype(np.int32) - ref.astype(np.int32)).max()))
+    return res
 
 
 def run_serve(args):

@@ -63,7 +63,7 @@ enum { L_EMPTY = 0, L_BRL = 1, L_IDL = 2, L_HQL = 3, L_NOCAND = 4 };
 // only with -DSKMMSE_PHASE_CLOCKS; the release build keeps the slots at zero.
 enum {
     PH_STAGE = 0, PH_CTX, PH_BRL, PH_IDL, PH_H0, PH_H1, PH_CHOL, PH_H2, PH_H3, PH_H4, PH_H5,
-    PH_HFIN, PH_WB, PH_PUB
+    PH_HFIN, PH_WB, PH_PUB, PH_X1, PH_X2  // X1, X2: spare slots for finer splits
 };
 #ifdef SKMMSE_PHASE_CLOCKS
 #define SK_PHASE(slot)                                           \
@@ -147,13 +147,20 @@ struct __align__(16) HqlP1 {                 // covariance / factorisation phase
     df32 A[32][33];
     df32 X[32][33];
 };
+constexpr int kI0Pad = 36;   // leave-one-out members padded to whole 3-member tiles
+constexpr int kVs = 44;      // row stride of a whitened chunk (conflict-free 16-byte reads)
 struct __align__(16) HqlP2 {                 // beta / leave-one-out phase
     union {
-        __align__(16) float Vs[kCh][kZs];    // whitened chunk: x'(4) u(32) 1 pad(3)
+        struct {
+            __align__(16) float Vs[kCh][kVs];      // whitened chunk: x'(4) u(32) 1 pad
+            __align__(16) float Wt[kCh][kI0Pad];   // leave-one-out weights, candidate-major
+        };
         float mrg[kThreads][37];             // per-thread partial sums before a merge
+        float accP[2][kI0Pad][40];           // leave-one-out sums of the two candidate halves
     };
-    float mI[kThreads];                      // per-thread running maxima (leave-one-out)
-    __align__(16) float UI[kMaxI0][36];
+    float mrow[kI0Pad];                      // running maximum score per member
+    float scl[kI0Pad];                       // rescaling of the member's sums for this chunk
+    __align__(16) float UI[kI0Pad][36];
     float XI[kMaxI0][4];
     float accI[kMaxI0][37];                  // merged leave-one-out sums: x'(4) u(32) sum w
 };
@@ -217,6 +224,10 @@ struct __align__(128) Smem {
     int nbent[9];
     int entry;
     int pad0;
+    struct {
+        int step, pa, pb, ny;
+        float phi, mean;
+    } hand;                            // step handed from warp 0 to the CTA
     unsigned long long st[kNStats];    // per-CTA counters
     TraceRec tr;                       // trace record of the current step
     long long ph_t;                    // last phase mark (SKMMSE_PHASE_CLOCKS)
@@ -365,15 +376,15 @@ __device__ __forceinline__ bool cand_valid(const Smem& sm, const StepCtx& c, int
 
 // squared Euclidean context distance of window (base = u*48+v), Eq. (15)
 __device__ __forceinline__ float ctx_dist(const float* S, const StepCtx& c, int base) {
-    float d = 0.0f;
+    float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // four partial sums: independent FMA chains
 #pragma unroll
     for (int k = 0; k < 36; ++k) {
         if ((c.ymask >> k) & 1ull) {
             const float t = c.y0w[k] - S[base + (k / 6) * kReg + (k % 6)];
-            d = __fmaf_rn(t, t, d);
+            d[k & 3] = __fmaf_rn(t, t, d[k & 3]);
         }
     }
-    return d;
+    return (d[0] + d[1]) + (d[2] + d[3]);
 }
 
 // ring k (1-based) enumeration: i-th position of the square annulus with Chebyshev
@@ -411,20 +422,73 @@ __device__ __forceinline__ void online_add(float s, float x0, float x1, float x2
     sx[3] = __fmaf_rn(w, x3, sx[3]);
 }
 
-__device__ __forceinline__ void slot_merge(float& m, float& s0, float sx[4], float m2, float s02,
-                                           const float sx2[4]) {
-    const float M = fmaxf(m, m2);
-    const float a = expf(m - M), b = expf(m2 - M);
-    s0 = s0 * a + s02 * b;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) sx[q] = sx[q] * a + sx2[q] * b;
-    m = M;
-}
-
 constexpr float kNegBig = -1.0e30f;
 
 // ------------------------------------------------------------------------------------
 // IDL: Eq. (15) over growing rings; returns 1 accepted, 0 not accepted, -1 no candidate
+
+// next patch (R2): the unfilled patch with the most available pixels in its 6x6 window,
+// ties to the lowest index.  Warp-level: every lane returns the same patch.
+__device__ __forceinline__ int select_patch(const Smem& sm, int lane) {
+    const unsigned long long uf = sm.unfilled;
+    int best = -1;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+        const int p = lane + 32 * h2;
+        if ((uf >> p) & 1ull) {
+            const int a = p >> 3, b = p & 7;
+            const int wr = kMB + 2 * a - 2, wc = kMB + 2 * b - 2;
+            int cnt = 0;
+#pragma unroll
+            for (int r = 0; r < 6; ++r) cnt += __popc((unsigned)(sm.av[wr + r] >> wc) & 63u);
+            best = max(best, cnt * 64 + (63 - p));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    return 63 - (best & 63);
+}
+
+struct CtxStats {
+    int ny;
+    float phi, mean;  // flatness (max - min) and mean of the context, Eqs. (16)-(17)
+};
+
+// context of the window at (wr, wc): size, flatness and mean.  Warp-level reductions; every
+// lane returns the same values.
+__device__ __forceinline__ CtxStats ctx_stats(const Smem& sm, int wr, int wc, int lane) {
+    unsigned long long ymask = 0;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) ymask |= (unsigned long long)((sm.av[wr + r] >> wc) & 63ull) << (6 * r);
+    float mx = -INFINITY, mn = INFINITY, sum = 0.0f;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+        const int k = lane + 32 * h2;
+        if (k < 36 && ((ymask >> k) & 1ull)) {
+            const float v = sm.S[(wr + k / 6) * kReg + wc + k % 6];
+            mx = fmaxf(mx, v);
+            mn = fminf(mn, v);
+            sum += v;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
+    CtxStats cs;
+    cs.ny = __popcll(ymask);
+    cs.phi = mx - mn;
+    cs.mean = cs.ny > 0 ? sum / (float)cs.ny : 0.0f;
+    return cs;
+}
+
+// The dynamic shared memory of the concealment kernel.  Out-of-line device functions take
+// their view of it from here rather than through a reference argument, so that the
+// compiler keeps every access in the shared address space.
+extern __shared__ __align__(128) unsigned char smem_raw[];
+__device__ __forceinline__ Smem& smem_ref() { return *reinterpret_cast<Smem*>(smem_raw); }
 
 // Not inlined, with scalar arguments: the 36 context values live in registers only while
 // this function runs, so the per-step loop of the kernel keeps a small register footprint.
@@ -436,8 +500,9 @@ struct IdlOut {
     int r;      // 1 accepted, 0 not accepted, -1 no candidate
 };
 
-__device__ __noinline__ IdlOut idl_step(Smem& sm, const KParams& P, int wr, int wc,
+__device__ __noinline__ IdlOut idl_step(const KParams& P, int wr, int wc,
                                         unsigned long long ymask, int ny, float mean) {
+    Smem& sm = smem_ref();
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     StepCtx c;
     c.wr = wr;
@@ -478,18 +543,19 @@ __device__ __noinline__ IdlOut idl_step(Smem& sm, const KParams& P, int wr, int 
                        s0, sx);
             ++cnt;
         }
-        // warp combine
-        float wm = m, ws = s0, wx[4] = {sx[0], sx[1], sx[2], sx[3]};
+        // warp combine: the maximum first, then one rescale per lane and plain sums
+        float wm = m;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+        const float lsc = expf(m - wm);
+        float ws = s0 * lsc, wx[4] = {sx[0] * lsc, sx[1] * lsc, sx[2] * lsc, sx[3] * lsc};
         int wc = cnt;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const float m2 = __shfl_xor_sync(0xffffffffu, wm, o);
-            const float s2 = __shfl_xor_sync(0xffffffffu, ws, o);
-            float x2[4];
+            ws += __shfl_xor_sync(0xffffffffu, ws, o);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) x2[q] = __shfl_xor_sync(0xffffffffu, wx[q], o);
+            for (int q = 0; q < 4; ++q) wx[q] += __shfl_xor_sync(0xffffffffu, wx[q], o);
             wc += __shfl_xor_sync(0xffffffffu, wc, o);
-            slot_merge(wm, ws, wx, m2, s2, x2);
         }
         IdlSlot* slot = &sm.idl[k & 1][0];
         if (lane == 0) {
@@ -500,12 +566,18 @@ __device__ __noinline__ IdlOut idl_step(Smem& sm, const KParams& P, int wr, int 
             slot[wid].cnt = wc;
         }
         __syncthreads();
-        float bm = slot[0].m, bs = slot[0].s0, bx[4] = {slot[0].sx[0], slot[0].sx[1],
-                                                        slot[0].sx[2], slot[0].sx[3]};
-        int bc = slot[0].cnt;
-        for (int w = 1; w < kWarps; ++w) {
-            const float x2[4] = {slot[w].sx[0], slot[w].sx[1], slot[w].sx[2], slot[w].sx[3]};
-            slot_merge(bm, bs, bx, slot[w].m, slot[w].s0, x2);
+        // CTA combine, the same way over the warps' slots
+        float bm = slot[0].m;
+#pragma unroll
+        for (int w = 1; w < kWarps; ++w) bm = fmaxf(bm, slot[w].m);
+        float bs = 0.0f, bx[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        int bc = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const float e = expf(slot[w].m - bm);
+            bs = __fmaf_rn(slot[w].s0, e, bs);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bx[q] = __fmaf_rn(slot[w].sx[q], e, bx[q]);
             bc += slot[w].cnt;
         }
         total_cnt = bc;
@@ -707,7 +779,8 @@ __device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, float shift) {
 
 // H1 on tensor cores: D[a][b] = sum_j z'_ja z'_jb and D[a][36] = sum_j z'_ja
 template <bool BF16>
-__device__ __noinline__ void h1_mixed(Smem& sm, int M, float shift, uint32_t tmem, uint32_t& mph) {
+__device__ __noinline__ void h1_mixed(int M, float shift, uint32_t tmem, uint32_t mph) {
+    Smem& sm = smem_ref();
     Hql& h = sm.hql;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nchunks = (M + kCh - 1) / kCh;
@@ -743,7 +816,8 @@ __device__ __noinline__ void h1_mixed(Smem& sm, int M, float shift, uint32_t tme
 
 // H2 on tensor cores: u_j = L^-1 (y_j - y0) for 64 candidates at a time, d_j = ||u_j||^2
 template <bool BF16>
-__device__ __noinline__ float h2_mixed(Smem& sm, int M, int ny, float shift, uint32_t tmem, uint32_t& mph) {
+__device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem, uint32_t mph) {
+    Smem& sm = smem_ref();
     Hql& h = sm.hql;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nchunks = (M + kCh - 1) / kCh;
@@ -794,8 +868,9 @@ __device__ __noinline__ float h2_mixed(Smem& sm, int M, int ny, float shift, uin
 
 // H3 on tensor cores: D[b][k] = sum_j w_j(b) z'_j[k] with w_j(b) = exp(-(d_j - dmin)/(2 beta_b))
 template <bool BF16>
-__device__ __noinline__ void h3_mixed(Smem& sm, const KParams& P, int M, float shift, float dmin,
-                                         uint32_t tmem, uint32_t& mph) {
+__device__ __noinline__ void h3_mixed(const KParams& P, int M, float shift, float dmin,
+                                         uint32_t tmem, uint32_t mph) {
+    Smem& sm = smem_ref();
     Hql& h = sm.hql;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nchunks = (M + kCh - 1) / kCh;
@@ -840,12 +915,14 @@ __device__ __noinline__ void h3_mixed(Smem& sm, const KParams& P, int M, float s
 // mean), so that the caller's per-step state stays in registers.
 struct HqlOut {
     float x[4];
+    uint32_t mph;  // tensor-core barrier phase after the step
 };
 
 template <int MIXED>
-__device__ __noinline__ HqlOut hql_step(Smem& sm, const KParams& P, int wr, int wc,
-                                        unsigned long long ymask, int ny, float mean,
-                                        TraceRec* tr, bool trace, uint32_t& mph) {
+__device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
+                                        unsigned long long ymask, int ny, float mean, bool trace,
+                                        uint32_t mph) {
+    Smem& sm = smem_ref();
     Hql& h = sm.hql;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nz = ny + 4;
@@ -897,9 +974,11 @@ __device__ __noinline__ HqlOut hql_step(Smem& sm, const KParams& P, int wr, int 
     SK_PHASE(PH_H0);
 
     if (MIXED == 1) {
-        h1_mixed<true>(sm, M, shift, sm.tmem_base, mph);
+        h1_mixed<true>(M, shift, sm.tmem_base, mph);
+        mph ^= (uint32_t)(nchunks & 1);
     } else if (MIXED == 2) {
-        h1_mixed<false>(sm, M, shift, sm.tmem_base, mph);
+        h1_mixed<false>(M, shift, sm.tmem_base, mph);
+        mph ^= (uint32_t)(nchunks & 1);
     } else
     // H1: sums of z' and z' z'^T, z' = z - shift (Eq. (8)).  Thread (a, g) owns row a of the
     // product matrix over the candidates j = g (mod kG1).  Integer parts multiply and
@@ -1088,9 +1167,11 @@ __device__ __noinline__ HqlOut hql_step(Smem& sm, const KParams& P, int wr, int 
     const int tj = (tid >> 3) * 2, tq = tid & 7;
     float lmin = INFINITY;
     if (MIXED == 1) {
-        lmin = h2_mixed<true>(sm, M, ny, shift, sm.tmem_base, mph);
+        lmin = h2_mixed<true>(M, ny, shift, sm.tmem_base, mph);
+        mph ^= (uint32_t)(nchunks & 1);
     } else if (MIXED == 2) {
-        lmin = h2_mixed<false>(sm, M, ny, shift, sm.tmem_base, mph);
+        lmin = h2_mixed<false>(M, ny, shift, sm.tmem_base, mph);
+        mph ^= (uint32_t)(nchunks & 1);
     } else {
         hql_stage(sm, 0, 0, min(kCh, M), shift);
         for (int ch = 0; ch < nchunks; ++ch) {
@@ -1139,9 +1220,11 @@ __device__ __noinline__ HqlOut hql_step(Smem& sm, const KParams& P, int wr, int 
     // Subset partial sums merge in double-float.
     const int nb = P.nbeta;
     if (MIXED == 1) {
-        h3_mixed<true>(sm, P, M, shift, dmin, sm.tmem_base, mph);
+        h3_mixed<true>(P, M, shift, dmin, sm.tmem_base, mph);
+        mph ^= (uint32_t)(nchunks & 1);
     } else if (MIXED == 2) {
-        h3_mixed<false>(sm, P, M, shift, dmin, sm.tmem_base, mph);
+        h3_mixed<false>(P, M, shift, dmin, sm.tmem_base, mph);
+        mph ^= (uint32_t)(nchunks & 1);
     } else {
         const int G3 = kThreads / nb;
         const int b = tid % nb, g = tid / nb;
@@ -1329,94 +1412,141 @@ __device__ __noinline__ HqlOut hql_step(Smem& sm, const KParams& P, int wr, int 
     // -||u_i - u_j||^2 / (2 beta*) (j != i) and the weighted sums of [x'_j | u_j | 1].
     float num = 0.0f, den = 0.0f;
     if (n0 > 0) {
-        constexpr int kG5 = kThreads / kMaxI0;
         const float ib = P.inv2beta[bstar];
-        const int mi = tid % kMaxI0, g = tid / kMaxI0;
-        const bool act = g < kG5 && mi < n0;
-        const int self = act ? h.i0[mi] : -1;
-        float ui[32];
+        const int nyq = (ny + 3) >> 2;
+        // scores: thread (it, jq) owns members 3it..3it+2 x candidates jq + 16r (r < 4)
+        const int it = tid >> 4, jq = tid & 15;
+        const bool sc_act = it < kI0Pad / 3;
+        int selfc[3];
 #pragma unroll
-        for (int k = 0; k < 32; ++k) ui[k] = act ? h.p2.UI[mi][k] : 0.0f;
-        float acc[37];
+        for (int a = 0; a < 3; ++a) {
+            const int i = 3 * it + a;
+            selfc[a] = (sc_act && i < n0) ? h.i0[i] : -2;  // -2: padding member (masked)
+        }
+        // sums: thread (ib4, kb, jg) owns members 4ib4..+3 x columns 4kb..+3 over candidates
+        // jg, jg + 2, ... of each chunk
+        const int jg = tid / 90, rr = tid - jg * 90, ib4 = rr / 10, kb = rr - ib4 * 10;
+        const bool ac_act = tid < 180;
+        float acc[4][4];
 #pragma unroll
-        for (int k = 0; k < 37; ++k) acc[k] = 0.0f;
-        float m = -INFINITY;
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][q] = 0.0f;
+        if (tid < kI0Pad) {
+            h.p2.mrow[tid] = -INFINITY;
+            if (tid >= n0)
+                for (int k = 0; k < 36; ++k) h.p2.UI[tid][k] = 0.0f;
+        }
         hql_stage(sm, 0, 0, min(kCh, M), shift);
         for (int ch = 0; ch < nchunks; ++ch) {
             const int buf = ch & 1, c0 = ch * kCh, n = min(kCh, M - c0);
-            __syncthreads();  // staged chunk visible; previous chunk's Vs consumed
+            __syncthreads();  // staged chunk visible; previous chunk's Vs / Wt consumed
             {
                 float u0[4], u1[4];
                 whiten_tile(h, buf, ny, tj, tq, u0, u1);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    h.p2.Vs[tj][4 + 4 * tq + q] = u0[q];
-                    h.p2.Vs[tj + 1][4 + 4 * tq + q] = u1[q];
-                }
+                *reinterpret_cast<float4*>(&h.p2.Vs[tj][4 + 4 * tq]) = make_float4(u0[0], u0[1], u0[2], u0[3]);
+                *reinterpret_cast<float4*>(&h.p2.Vs[tj + 1][4 + 4 * tq]) = make_float4(u1[0], u1[1], u1[2], u1[3]);
                 if (tq == 0) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         h.p2.Vs[tj][q] = h.Z[buf][tj][q];
                         h.p2.Vs[tj + 1][q] = h.Z[buf][tj + 1][q];
                     }
-                    h.p2.Vs[tj][36] = h.Z[buf][tj][36];
-                    h.p2.Vs[tj + 1][36] = h.Z[buf][tj + 1][36];
+                } else if (tq == 1) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        h.p2.Vs[tj][36 + q] = q == 0 ? h.Z[buf][tj][36] : 0.0f;
+                        h.p2.Vs[tj + 1][36 + q] = q == 0 ? h.Z[buf][tj + 1][36] : 0.0f;
+                    }
                 }
             }
             __syncthreads();
+            SK_PHASE(PH_X1);
             if (ch + 1 < nchunks) hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), shift);
-            if (act) {
-                for (int j = g; j < n; j += kG5) {
-                    const float* v = &h.p2.Vs[j][0];
-                    float d = 0.0f;
+            // squared whitened distances, scores, chunk maxima and weights (Eq. (12) with
+            // candidate i left out)
+            if (sc_act) {
+                float d[3][4];
 #pragma unroll
-                    for (int k4 = 0; k4 < 8; ++k4) {
-                        const float4 q = *reinterpret_cast<const float4*>(&v[4 + 4 * k4]);
-                        float t;
-                        t = ui[4 * k4 + 0] - q.x; d = __fmaf_rn(t, t, d);
-                        t = ui[4 * k4 + 1] - q.y; d = __fmaf_rn(t, t, d);
-                        t = ui[4 * k4 + 2] - q.z; d = __fmaf_rn(t, t, d);
-                        t = ui[4 * k4 + 3] - q.w; d = __fmaf_rn(t, t, d);
-                    }
-                    if (c0 + j == self) continue;
-                    const float s = -d * ib;
-                    if (s > m) {
-                        const float sc = expf(m - s);
+                for (int a = 0; a < 3; ++a)
 #pragma unroll
-                        for (int k = 0; k < 37; ++k) acc[k] *= sc;
-                        m = s;
-                    }
-                    const float w = expf(s - m);
+                    for (int r = 0; r < 4; ++r) d[a][r] = 0.0f;
+                for (int l4 = 0; l4 < nyq; ++l4) {
+                    float4 ua[3], vb[4];
 #pragma unroll
-                    for (int k4 = 0; k4 < 9; ++k4) {
-                        const float4 q = *reinterpret_cast<const float4*>(&v[4 * k4]);
-                        acc[4 * k4 + 0] = __fmaf_rn(w, q.x, acc[4 * k4 + 0]);
-                        acc[4 * k4 + 1] = __fmaf_rn(w, q.y, acc[4 * k4 + 1]);
-                        acc[4 * k4 + 2] = __fmaf_rn(w, q.z, acc[4 * k4 + 2]);
-                        acc[4 * k4 + 3] = __fmaf_rn(w, q.w, acc[4 * k4 + 3]);
+                    for (int a = 0; a < 3; ++a) ua[a] = *reinterpret_cast<const float4*>(&h.p2.UI[3 * it + a][4 * l4]);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) vb[r] = *reinterpret_cast<const float4*>(&h.p2.Vs[jq + 16 * r][4 + 4 * l4]);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            float t;
+                            t = ua[a].x - vb[r].x; d[a][r] = __fmaf_rn(t, t, d[a][r]);
+                            t = ua[a].y - vb[r].y; d[a][r] = __fmaf_rn(t, t, d[a][r]);
+                            t = ua[a].z - vb[r].z; d[a][r] = __fmaf_rn(t, t, d[a][r]);
+                            t = ua[a].w - vb[r].w; d[a][r] = __fmaf_rn(t, t, d[a][r]);
+                        }
+                }
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    float sc[4];
+                    float mx = -INFINITY;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int j = jq + 16 * r;
+                        const bool ok = j < n && c0 + j != selfc[a] && selfc[a] != -2;
+                        sc[r] = ok ? -d[a][r] * ib : -INFINITY;
+                        mx = fmaxf(mx, sc[r]);
                     }
-                    acc[36] += w;
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                    const int i = 3 * it + a;
+                    const float mold = h.p2.mrow[i];
+                    const float mnew = fmaxf(mold, mx);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        h.p2.Wt[jq + 16 * r][i] = sc[r] == -INFINITY ? 0.0f : expf(sc[r] - mnew);
+                    __syncwarp();
+                    if (jq == 0) {
+                        h.p2.scl[i] = mold == -INFINITY ? 0.0f : expf(mold - mnew);
+                        h.p2.mrow[i] = mnew;
+                    }
+                }
+            }
+            __syncthreads();
+            SK_PHASE(PH_X2);
+            // weighted sums of [x' | u | 1] (online, rescaled by the new maxima)
+            if (ac_act) {
+                const float4 s4 = *reinterpret_cast<const float4*>(&h.p2.scl[4 * ib4]);
+                const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[a][q] *= sv[a];
+                for (int j = jg; j < n; j += 2) {
+                    const float4 w4 = *reinterpret_cast<const float4*>(&h.p2.Wt[j][4 * ib4]);
+                    const float4 v4 = *reinterpret_cast<const float4*>(&h.p2.Vs[j][4 * kb]);
+                    const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+                    const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[a][q] = __fmaf_rn(wv[a], vv[q], acc[a][q]);
                 }
             }
         }
-        __syncthreads();  // Vs no longer needed: its storage takes the partial sums
-        if (act) {
+        __syncthreads();  // Vs / Wt no longer needed: their storage takes the partial sums
+        if (ac_act) {
 #pragma unroll
-            for (int k = 0; k < 37; ++k) h.p2.mrg[tid][k] = acc[k];
-            h.p2.mI[tid] = m;
+            for (int a = 0; a < 4; ++a)
+                *reinterpret_cast<float4*>(&h.p2.accP[jg][4 * ib4 + a][4 * kb]) =
+                    make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
         }
         __syncthreads();
-        // merge the subsets of each member with the max-subtracted rescaling
         for (int idx = tid; idx < n0 * 37; idx += kThreads) {
-            const int i = idx / 37, k = idx % 37;
-            float mm = -INFINITY;
-            for (int gg = 0; gg < kG5; ++gg) mm = fmaxf(mm, h.p2.mI[gg * kMaxI0 + i]);
-            float sacc = 0.0f;
-            for (int gg = 0; gg < kG5; ++gg) {
-                const float mg = h.p2.mI[gg * kMaxI0 + i];
-                if (mg > -INFINITY) sacc += h.p2.mrg[gg * kMaxI0 + i][k] * expf(mg - mm);
-            }
-            h.p2.accI[i][k] = sacc;
+            const int i = idx / 37, k = idx - (idx / 37) * 37;
+            h.p2.accI[i][k] = h.p2.accP[0][i][k] + h.p2.accP[1][i][k];
         }
         __syncthreads();
         // r_i = x_i - x~_i ; g_i = G (u_i - u~_i) ; alpha = sum r.g / sum g.g
@@ -1457,23 +1587,24 @@ __device__ __noinline__ HqlOut hql_step(Smem& sm, const KParams& P, int wr, int 
     const float alpha = h.alpha;
     // x0_hat = x~0 + alpha C_XY C_YY^-1 (y0 - y~0), Eq. (13)
     HqlOut out;
+    out.mph = mph;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const df32 v = df_add(df_add(df_make(shift), h.xt0d[a]), df_mul_f(h.corr[a], alpha));
         out.x[a] = df_to_f(v);
     }
     if (trace && tid == 0) {
-        tr->beta_idx = (int8_t)bstar;
-        tr->n0 = (int8_t)n0;
-        tr->alpha = alpha;
-        tr->eps_best = h.eps[bstar];
-        tr->m = (int16_t)M;
+        sm.tr.beta_idx = (int8_t)bstar;
+        sm.tr.n0 = (int8_t)n0;
+        sm.tr.alpha = alpha;
+        sm.tr.eps_best = h.eps[bstar];
+        sm.tr.m = (int16_t)M;
         for (int t = 0; t < 36; ++t) {
             if (t < n0) {
                 const int base = h.cand[h.i0[t]];
-                tr->i0[t] = (uint16_t)((base / kReg) * kNpos + base % kReg);
+                sm.tr.i0[t] = (uint16_t)((base / kReg) * kNpos + base % kReg);
             } else {
-                tr->i0[t] = 0xffff;
+                sm.tr.i0[t] = 0xffff;
             }
         }
     }
@@ -1593,8 +1724,7 @@ __device__ __noinline__ void release_dependants(const WorkDev& W, const FrameDev
 template <int MIXED>
 __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_constant__ WorkDev W,
                                                               const __grid_constant__ KParams P) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+    Smem& sm = smem_ref();
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const bool trace_on = (P.flags & 1u) != 0u;
     const bool force_on = (P.flags & 2u) != 0u;
@@ -1715,31 +1845,78 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
         TraceRec* trace_base =
             (trace_on && F.trace) ? reinterpret_cast<TraceRec*>(F.trace) + (size_t)ent.z * 64 : nullptr;
         const int npatch = __popcll(sm.unfilled);
-        for (int step = 0; step < npatch; ++step) {
-            StepCtx c;
-            // next patch (R2): most available pixels in the 6x6 window, lowest index
-            {
-                const unsigned long long uf = sm.unfilled;
-                int best = -1;
-#pragma unroll
-                for (int h2 = 0; h2 < 2; ++h2) {
-                    const int p = lane + 32 * h2;
-                    if ((uf >> p) & 1ull) {
-                        const int a = p >> 3, b = p & 7;
-                        const int wr = kMB + 2 * a - 2, wc = kMB + 2 * b - 2;
-                        int cnt = 0;
-#pragma unroll
-                        for (int r = 0; r < 6; ++r) cnt += __popc((unsigned)(sm.av[wr + r] >> wc) & 63u);
-                        const int key = cnt * 64 + (63 - p);
-                        best = max(best, key);
+        int step = 0;
+        for (;;) {
+            // Warp 0 alone runs the steps that stay in the base layer (Eq. (16), R3) back to
+            // back; it stops at the first step that needs IDL and hands it to the CTA.
+            if (wid == 0) {
+                long long n_brl = 0, n_empty = 0, flops = 0;
+                for (; step < npatch; ++step) {
+                    const int p = select_patch(sm, lane);
+                    const int pa = p >> 3, pb = p & 7;
+                    const int wr = kMB + 2 * pa - 2, wc = kMB + 2 * pb - 2;
+                    const CtxStats cs = ctx_stats(sm, wr, wc, lane);
+                    if (lane == 0) {
+                        sm.hand.pa = pa;
+                        sm.hand.pb = pb;
+                        sm.hand.ny = cs.ny;
+                        sm.hand.phi = cs.phi;
+                        sm.hand.mean = cs.mean;
                     }
+                    SK_PHASE(PH_CTX);
+                    if (cs.ny > 0 && cs.phi > P.t_phi) break;
+                    const float xv = cs.ny == 0 ? 128.0f : cs.mean;
+                    const int pr = wr + 2, pc = wc + 2;
+                    if (lane < 4) {
+                        float xw = fminf(fmaxf(xv, 0.0f), 255.0f);
+                        if (force_on && trace_base) xw = trace_base[step].x[lane];  // verification hook
+                        sm.S[(pr + (lane >> 1)) * kReg + pc + (lane & 1)] = xw;
+                    }
+                    if (lane == 0) {
+                        sm.av[pr] |= 3ull << pc;
+                        sm.av[pr + 1] |= 3ull << pc;
+                        sm.unfilled &= ~(1ull << p);
+                        if (cs.ny == 0) ++n_empty;
+                        else ++n_brl;
+                        flops += 3ll * cs.ny;
+                        if (trace_base) {
+                            TraceRec t;
+                            t.mb = mb;
+                            t.step = (int16_t)step;
+                            t.patch = (int16_t)p;
+                            t.layer = (int8_t)(cs.ny == 0 ? L_EMPTY : L_BRL);
+                            t.ring = 0;
+                            t.beta_idx = -1;
+                            t.n0 = 0;
+                            t.ny = (int16_t)cs.ny;
+                            t.m = 0;
+                            t.phi = cs.phi;
+                            t.log_nu = -INFINITY;
+                            t.alpha = 0.0f;
+                            t.eps_best = 0.0f;
+                            for (int a = 0; a < 4; ++a) t.x[a] = fminf(fmaxf(xv, 0.0f), 255.0f);
+                            for (int q = 0; q < 36; ++q) t.i0[q] = 0xffff;
+                            trace_base[step] = t;
+                        }
+                    }
+                    __syncwarp();
+                    SK_PHASE(PH_BRL);
                 }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
-                const int p = 63 - (best & 63);
-                c.pa = p >> 3;
-                c.pb = p & 7;
+                if (lane == 0) {
+                    sm.hand.step = step;
+                    sm.st[ST_PATCH] += n_brl + n_empty;
+                    sm.st[ST_BRL] += n_brl;
+                    sm.st[ST_EMPTY] += n_empty;
+                    sm.st[ST_FLOPS] += flops;
+                }
             }
+            __syncthreads();
+            step = sm.hand.step;
+            if (step >= npatch) break;
+
+            StepCtx c;
+            c.pa = sm.hand.pa;
+            c.pb = sm.hand.pb;
             c.wr = kMB + 2 * c.pa - 2;
             c.wc = kMB + 2 * c.pb - 2;
             c.ymask = 0;
@@ -1747,23 +1924,11 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
             for (int r = 0; r < 6; ++r) {
                 const unsigned bits = (unsigned)(sm.av[c.wr + r] >> c.wc) & 63u;
                 c.ymask |= (unsigned long long)bits << (6 * r);
-                c.rowcfg[r] = bits | ((r == 2 || r == 3) ? 12u : 0u);
             }
-            c.ny = __popcll(c.ymask);
-            float mx = -INFINITY, mn = INFINITY, sum = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 36; ++k) {
-                const float v = sm.S[(c.wr + k / 6) * kReg + c.wc + k % 6];
-                if ((c.ymask >> k) & 1ull) {
-                    mx = fmaxf(mx, v);
-                    mn = fminf(mn, v);
-                    sum += v;
-                }
-            }
-            c.phi = mx - mn;
-            c.mean = c.ny > 0 ? sum / (float)c.ny : 0.0f;
+            c.ny = sm.hand.ny;
+            c.phi = sm.hand.phi;
+            c.mean = sm.hand.mean;
 
-            SK_PHASE(PH_CTX);
             float xhat[4];
             int layer;
             int ring = 0;
@@ -1777,14 +1942,8 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                 sm.tr.m = 0;
                 for (int t = 0; t < 36; ++t) sm.tr.i0[t] = 0xffff;
             }
-            if (c.ny == 0) {
-                layer = L_EMPTY;  // R3
-                xhat[0] = xhat[1] = xhat[2] = xhat[3] = 128.0f;
-            } else if (c.phi <= P.t_phi) {
-                layer = L_BRL;    // Eq. (16)
-                xhat[0] = xhat[1] = xhat[2] = xhat[3] = c.mean;
-            } else {
-                const IdlOut io = idl_step(sm, P, c.wr, c.wc, c.ymask, c.ny, c.mean);
+            {
+                const IdlOut io = idl_step(P, c.wr, c.wc, c.ymask, c.ny, c.mean);
                 const int r = io.r;
                 ring = io.ring;
                 lognu = io.lognu;
@@ -1806,13 +1965,13 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                 } else {
                     layer = L_HQL;
                     __syncthreads();  // IDL slots -> HQL scratch
-                    const HqlOut o = hql_step<MIXED>(sm, P, c.wr, c.wc, c.ymask, c.ny, c.mean, &sm.tr,
+                    const HqlOut o = hql_step<MIXED>(P, c.wr, c.wc, c.ymask, c.ny, c.mean,
                                                      trace_base != nullptr, mph);
+                    mph = o.mph;
 #pragma unroll
                     for (int a = 0; a < 4; ++a) xhat[a] = o.x[a];
                 }
             }
-            if (layer == L_EMPTY || layer == L_BRL) SK_PHASE(PH_BRL);
             // R8: clip and write back
             if (tid == 0) {
                 const int pr = c.wr + 2, pc = c.wc + 2;
@@ -1832,8 +1991,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                 sm.unfilled &= ~(1ull << (c.pa * 8 + c.pb));
                 sm.st[ST_PATCH] += 1;
                 sm.st[ST_FLOPS] += 3ull * c.ny;  // context gather, flatness, mean
-                sm.st[layer == L_EMPTY ? ST_EMPTY : layer == L_BRL ? ST_BRL : layer == L_IDL ? ST_IDL
-                      : layer == L_HQL ? ST_HQL : ST_NOCAND] += 1;
+                sm.st[layer == L_IDL ? ST_IDL : layer == L_HQL ? ST_HQL : ST_NOCAND] += 1;
                 if (layer == L_IDL) sm.st[ST_RING0 + min(ring, 15)] += 1;
                 if (trace_base) {
                     TraceRec& t = sm.tr;
@@ -1851,6 +2009,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
             }
             __syncthreads();
             SK_PHASE(PH_WB);
+            ++step;
         }
 
         // publish: unrounded values for dependants, rounded / FP32 outputs

@@ -258,7 +258,7 @@ class Context:
         _check(self._lib.skmmse_set_ctas_per_sm(self._h, int(k)), "skmmse_set_ctas_per_sm")
 
     PHASES = ["stage", "ctx", "brl", "idl", "h_cand", "h_cov", "h_chol", "h_dist", "h_beta",
-              "h_i0", "h_alpha", "h_est", "writeback", "publish"]
+              "h_i0", "h_alpha", "h_est", "writeback", "publish", "x1", "x2"]
 
     def read_phase_clocks(self, stream=None) -> dict:
         """Per-phase SM cycles of the last call (library built with SKMMSE_PHASE_CLOCKS)."""

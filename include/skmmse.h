@@ -61,9 +61,13 @@ typedef enum {
                                    skmmse_conceal_noalloc (SKMMSE_NOALLOC_MAX_MBS blocks) */
 } skmmse_status;
 
-/* Arithmetic of the distance contraction.  FP32: every step in FP32 on the CUDA cores
-   (HQL covariance and Cholesky with exact/compensated FP32 arithmetic).  The mixed modes
-   run the template-distance contractions on tcgen05 tensor cores. */
+/* Arithmetic of the HQL contractions (Eqs. (7)-(10)).  FP32: every step in FP32 on the
+   CUDA cores (covariance with exact integer parts, factorisation in double-float).  The
+   mixed modes run the covariance, the whitened (Mahalanobis) distances and the beta-grid
+   sums on tcgen05 tensor cores with FP32 accumulation: integer parts of the covariance
+   exactly, every other operand split into a high and a low 16-bit half.  Exponentials,
+   normalisations, the IDL layer and the leave-one-out pass stay FP32.  Teacher-forced per
+   step against an FP64 reference: FP16 within ~2e-3 gray, BF16 within ~4e-2 gray. */
 typedef enum { SKMMSE_FP32 = 0, SKMMSE_MIXED_BF16 = 1, SKMMSE_MIXED_FP16 = 2 } skmmse_precision;
 
 /* Profiles of Table I (T_phi, T_nu): express (20, 0.01), efficient (20, 0.1),

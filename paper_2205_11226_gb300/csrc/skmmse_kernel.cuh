@@ -160,9 +160,6 @@ struct __align__(16) HqlP2 {                 // beta / leave-one-out phase
     };
     float mrow[kI0Pad];                      // running maximum score per member
     float scl[kI0Pad];                       // rescaling of the member's sums for this chunk
-    __align__(16) float UI[kI0Pad][36];
-    float XI[kMaxI0][4];
-    float accI[kMaxI0][37];                  // merged leave-one-out sums: x'(4) u(32) sum w
 };
 
 struct __align__(16) Hql {
@@ -172,7 +169,6 @@ struct __align__(16) Hql {
     float G[4][32];
     df32 cxy[4][32];            // C_XY (double-float)
     df32 K[4][32];              // C_XY C_YY^-1 (double-float)
-    df32 accBd[kMaxBeta][kZs];  // beta-pass sums (double-float)
     __align__(16) float ys[36];  // y0 - shift (compacted)
     short off[36];              // compacted context offsets rel. window top-left
     int i0[kMaxI0];             // I0 candidate indices, ascending
@@ -191,7 +187,11 @@ struct __align__(16) Hql {
     int koff[kZs];
     float lam;
     float alpha;
+    __align__(16) float UI[kI0Pad][36];      // whitened I0 members, u_i = L^-1 (y_i - y0)
+    float XI[kMaxI0][4];                     // x_i - shift of the I0 members
+    float accI[kMaxI0][37];                  // merged leave-one-out sums: x'(4) u(32) sum w
     union {
+        df32 accBd[kMaxBeta][kZs];  // beta-pass sums (double-float), end of H3 only
         struct {  // CUDA-core staging and phase buffers
             __align__(16) float Z[2][kCh][kZs];  // staged candidates, centred by the integer shift
             union {
@@ -717,6 +717,33 @@ __device__ __forceinline__ void store8_split(uint16_t* thi, uint16_t* tlo, int r
     *reinterpret_cast<uint4*>(tlo + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// 8 consecutive K values of row r, split into the integer part n = rint(v) (exact in both
+// 16-bit formats for |n| <= 256) and the fraction f = v - n as a high and a low 16-bit half
+template <bool BF16>
+__device__ __forceinline__ void store8_int_frac(uint16_t* tn, uint16_t* tfh, uint16_t* tfl, int r,
+                                                int k0, int K, const float v[8]) {
+    uint32_t n[4], fh[4], fl[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint16_t a[2], b[2], c[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const float x = v[2 * q + t];
+            const float xn = rintf(x);
+            uint16_t dummy;
+            split16<BF16>(xn, a[t], dummy);
+            split16<BF16>(x - xn, b[t], c[t]);
+        }
+        n[q] = (uint32_t)a[0] | ((uint32_t)a[1] << 16);
+        fh[q] = (uint32_t)b[0] | ((uint32_t)b[1] << 16);
+        fl[q] = (uint32_t)c[0] | ((uint32_t)c[1] << 16);
+    }
+    const uint32_t off = tc::kmajor_offset(r, k0, K) >> 1;
+    *reinterpret_cast<uint4*>(tn + off) = make_uint4(n[0], n[1], n[2], n[3]);
+    *reinterpret_cast<uint4*>(tfh + off) = make_uint4(fh[0], fh[1], fh[2], fh[3]);
+    *reinterpret_cast<uint4*>(tfl + off) = make_uint4(fl[0], fl[1], fl[2], fl[3]);
+}
+
 __device__ __forceinline__ void zero_tiles(Hql& h) {
     uint4* p = reinterpret_cast<uint4*>(&h.mx);
     for (int i = threadIdx.x; i < (int)(sizeof(h.mx) / 16); i += kThreads) p[i] = make_uint4(0, 0, 0, 0);
@@ -756,11 +783,14 @@ __device__ __forceinline__ void mma_round(Smem& sm, uint32_t& mph, IssueF issue)
 
 // stage rows 0..36 of Z^T for candidates [c0, c0+n): z' (feature rows 0..35, zero beyond
 // nz) and the constant one (row 36)
-template <bool BF16>
+template <bool BF16, bool INTFRAC>
 __device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, float shift) {
     Hql& h = sm.hql;
-    for (int idx = threadIdx.x; idx < 37 * 8; idx += kThreads) {
-        const int a = idx >> 3, g8 = idx & 7;
+    // a quarter-warp writes one 16-byte column group of 8 consecutive rows: one 128-byte
+    // core matrix, free of bank conflicts
+    for (int idx = threadIdx.x; idx < 40 * 8; idx += kThreads) {
+        const int a = ((idx >> 6) << 3) | (idx & 7), g8 = (idx >> 3) & 7;
+        if (a > 36) continue;
         const int ka = a < kZs ? h.koff[a] : -1;
         float v[8];
 #pragma unroll
@@ -773,43 +803,76 @@ __device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, float shift) {
             }
             v[t] = x;
         }
-        store8_split<BF16>(h.mx.t0, h.mx.t1, a, 8 * g8, 64, v);
+        if (INTFRAC) store8_int_frac<BF16>(h.mx.t0, h.mx.t1, h.mx.t2, a, 8 * g8, 64, v);
+        else store8_split<BF16>(h.mx.t0, h.mx.t1, a, 8 * g8, 64, v);
     }
 }
 
-// H1 on tensor cores: D[a][b] = sum_j z'_ja z'_jb and D[a][36] = sum_j z'_ja
+// H1 on tensor cores: D[a][b] = sum_j z'_ja z'_jb and D[a][36] = sum_j z'_ja, with
+// z' = n + f (integer part n, fraction f = fh + fl).  The integer products n_a n_b are
+// exact in 16 bits and their sum over 4 chunks (256 candidates, |n| <= 255: at most
+// 16,646,400) stays below 2^24, so the FP32 accumulator holds it exactly; it is read out
+// every 4 chunks into int32.  The
+// fractional cross terms n f + f n + f f accumulate in FP32 in a second accumulator
+// (tensor memory columns 64..111).  The same integer / fraction split as the CUDA-core
+// path, so the covariance keeps its precision through the cancellation in Eq. (8).
 template <bool BF16>
 __device__ __noinline__ void h1_mixed(int M, float shift, uint32_t tmem, uint32_t mph) {
     Smem& sm = smem_ref();
     Hql& h = sm.hql;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nchunks = (M + kCh - 1) / kCh;
+    const uint32_t idesc = tc::idesc_f16(128, 48, BF16);
     __syncthreads();  // the tiles share storage with buffers of the previous phase
     zero_tiles(h);
     __syncthreads();
+    const int arow = 32 * wid + lane;  // warps 0, 1: the row of D this thread reads
+    int ni[37];
+#pragma unroll
+    for (int b = 0; b < 37; ++b) ni[b] = 0;
     for (int ch = 0; ch < nchunks; ++ch) {
         const int c0 = ch * kCh, n = min(kCh, M - c0);
-        stage_zt<BF16>(sm, c0, n, shift);
-        mma_round(sm, mph, [&]() { mma3(tmem, h.mx.t0, h.mx.t1, h.mx.t0, h.mx.t1, 64, tc::idesc_f16(128, 48, BF16), ch > 0); });
+        stage_zt<BF16, true>(sm, c0, n, shift);
+        mma_round(sm, mph, [&]() {
+            const uint32_t sbo = (64 / 8) * 128;
+            const uint32_t an = tc::smem_addr(h.mx.t0), ah = tc::smem_addr(h.mx.t1),
+                           al = tc::smem_addr(h.mx.t2);
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t o = (uint32_t)kk * 256u;
+                const uint64_t dn = tc::smem_desc(an + o, 128, sbo), dh = tc::smem_desc(ah + o, 128, sbo),
+                               dl = tc::smem_desc(al + o, 128, sbo);
+                tc::mma_f16(tmem, dn, dn, idesc, (ch & 3) != 0 || kk > 0);  // integer part: 4 chunks
+                tc::mma_f16(tmem + 64, dn, dh, idesc, ch > 0 || kk > 0);
+                tc::mma_f16(tmem + 64, dh, dn, idesc, true);
+                tc::mma_f16(tmem + 64, dn, dl, idesc, true);
+                tc::mma_f16(tmem + 64, dl, dn, idesc, true);
+                tc::mma_f16(tmem + 64, dh, dh, idesc, true);
+            }
+        });
+        if (wid < 2 && ((ch & 3) == 3 || ch == nchunks - 1)) {  // exact sums into int32
+            float D[48];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 8 * c, &D[8 * c]);
+#pragma unroll
+            for (int b = 0; b < 37; ++b) ni[b] += __float2int_rn(D[b]);
+        }
+        // (the next chunk's mma_round orders these tensor-memory reads before its MMAs)
     }
-    float D[48];
+    float F[48];
     if (wid < 2) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 8 * c, &D[8 * c]);
+        for (int c = 0; c < 6; ++c) tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 64 + 8 * c, &F[8 * c]);
     }
     tc::fence_before();
     __syncthreads();  // the tiles are dead: their storage takes the sums
-    if (wid < 2) {
-        const int a = 32 * wid + lane;
-        if (a < 36) {
+    if (wid < 2 && arow < 36) {
 #pragma unroll
-            for (int b = 0; b < 36; ++b) {
-                h.p1.cint[a][b] = 0;
-                h.p1.cfrac[a][b] = D[b];
-            }
-            h.colNi[a] = 0;
-            h.colF[a] = D[36];
+        for (int b = 0; b < 36; ++b) {
+            h.p1.cint[arow][b] = ni[b];
+            h.p1.cfrac[arow][b] = F[b];
         }
+        h.colNi[arow] = ni[36];
+        h.colF[arow] = F[36];
     }
     __syncthreads();
 }
@@ -826,7 +889,7 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
     __syncthreads();
     // B = L^-1 (32 rows k x 32 columns l), staged once into t2/t3
     if (tid < 128) {
-        const int k = tid >> 2, l8 = tid & 3;
+        const int k = (tid & 7) | ((tid >> 5) << 3), l8 = (tid >> 3) & 3;  // conflict-free stores
         float v[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) v[t] = h.Linv[k][8 * l8 + t];
@@ -835,8 +898,9 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
     float lmin = INFINITY;
     for (int ch = 0; ch < nchunks; ++ch) {
         const int c0 = ch * kCh, n = min(kCh, M - c0);
-        {  // A = E (rows: candidates, columns: context), one task per thread
-            const int j = tid >> 2, l8 = tid & 3;
+        {  // A = E (rows: candidates, columns: context), one task per thread; a quarter-warp
+           // stores 8 consecutive rows of one column group (conflict-free)
+            const int j = (tid & 7) | ((tid >> 5) << 3), l8 = (tid >> 3) & 3;
             float v[8];
             const int base = j < n ? h.cand[c0 + j] : 0;
 #pragma unroll
@@ -880,9 +944,10 @@ __device__ __noinline__ void h3_mixed(const KParams& P, int M, float shift, floa
     __syncthreads();
     for (int ch = 0; ch < nchunks; ++ch) {
         const int c0 = ch * kCh, n = min(kCh, M - c0);
-        stage_zt<BF16>(sm, c0, n, shift);
-        {  // A = W (rows: beta, columns: candidates), one task per thread
-            const int b = tid >> 3, g8 = tid & 7;
+        stage_zt<BF16, false>(sm, c0, n, shift);
+        {  // A = W (rows: beta, columns: candidates), one task per thread; a quarter-warp
+           // stores 8 consecutive rows of one column group (conflict-free)
+            const int b = (tid & 7) | ((tid >> 6) << 3), g8 = (tid >> 3) & 7;
             if (b < nb) {
                 float v[8];
                 const float ib = P.inv2beta[b];
@@ -1397,10 +1462,10 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
                 if (k < ny)
                     for (int l = 0; l <= k; ++l)
                         u = __fmaf_rn(h.Linv[k][l], (sm.S[base + h.off[l]] - shift) - h.ys[l], u);
-                h.p2.UI[i][k] = u;
+                h.UI[i][k] = u;
             } else {
                 const int a = k - 32;
-                h.p2.XI[i][a] = sm.S[base + (a >> 1) * kReg + (a & 1) + 2 * kReg + 2] - shift;
+                h.XI[i][a] = sm.S[base + (a >> 1) * kReg + (a & 1) + 2 * kReg + 2] - shift;
             }
         }
     }
@@ -1435,7 +1500,7 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
         if (tid < kI0Pad) {
             h.p2.mrow[tid] = -INFINITY;
             if (tid >= n0)
-                for (int k = 0; k < 36; ++k) h.p2.UI[tid][k] = 0.0f;
+                for (int k = 0; k < 36; ++k) h.UI[tid][k] = 0.0f;
         }
         hql_stage(sm, 0, 0, min(kCh, M), shift);
         for (int ch = 0; ch < nchunks; ++ch) {
@@ -1474,7 +1539,7 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
                 for (int l4 = 0; l4 < nyq; ++l4) {
                     float4 ua[3], vb[4];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) ua[a] = *reinterpret_cast<const float4*>(&h.p2.UI[3 * it + a][4 * l4]);
+                    for (int a = 0; a < 3; ++a) ua[a] = *reinterpret_cast<const float4*>(&h.UI[3 * it + a][4 * l4]);
 #pragma unroll
                     for (int r = 0; r < 4; ++r) vb[r] = *reinterpret_cast<const float4*>(&h.p2.Vs[jq + 16 * r][4 + 4 * l4]);
 #pragma unroll
@@ -1546,18 +1611,18 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
         __syncthreads();
         for (int idx = tid; idx < n0 * 37; idx += kThreads) {
             const int i = idx / 37, k = idx - (idx / 37) * 37;
-            h.p2.accI[i][k] = h.p2.accP[0][i][k] + h.p2.accP[1][i][k];
+            h.accI[i][k] = h.p2.accP[0][i][k] + h.p2.accP[1][i][k];
         }
         __syncthreads();
         // r_i = x_i - x~_i ; g_i = G (u_i - u~_i) ; alpha = sum r.g / sum g.g
         if (tid < 4 * kMaxI0) {
             const int i = tid >> 2, a = tid & 3;
             if (i < n0) {
-                const float inv = 1.0f / h.p2.accI[i][36];
-                const float r = h.p2.XI[i][a] - h.p2.accI[i][a] * inv;
+                const float inv = 1.0f / h.accI[i][36];
+                const float r = h.XI[i][a] - h.accI[i][a] * inv;
                 float gg = 0.0f;
                 for (int k = 0; k < ny; ++k)
-                    gg = __fmaf_rn(h.G[a][k], h.p2.UI[i][k] - h.p2.accI[i][4 + k] * inv, gg);
+                    gg = __fmaf_rn(h.G[a][k], h.UI[i][k] - h.accI[i][4 + k] * inv, gg);
                 num = r * gg;
                 den = gg * gg;
             }
@@ -1721,6 +1786,10 @@ __device__ __noinline__ void release_dependants(const WorkDev& W, const FrameDev
     }
 }
 
+// tensor-memory columns per CTA: H1 uses 0..111
+template <int MIXED>
+constexpr uint32_t kTmemCols = 128u;
+
 template <int MIXED>
 __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_constant__ WorkDev W,
                                                               const __grid_constant__ KParams P) {
@@ -1736,7 +1805,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int i = tid; i < kNStats; i += kThreads) sm.st[i] = 0;
-    if (MIXED && wid == 0) tc::tmem_alloc(&sm.tmem_base, 64);  // 128 lanes x 64 FP32 columns
+    if (MIXED && wid == 0) tc::tmem_alloc(&sm.tmem_base, kTmemCols<MIXED>);  // 128 lanes x FP32 columns
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -2034,7 +2103,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (MIXED && wid == 0) tc::tmem_dealloc(sm.tmem_base, 64);
+    if (MIXED && wid == 0) tc::tmem_dealloc(sm.tmem_base, kTmemCols<MIXED>);
     if (tid == 0 && sm.mma_err) atomicExch(&W.counters[2], 6);
     for (int i = tid; i < kNStats; i += kThreads)
         if (sm.st[i]) atomicAdd(&W.stats[i], sm.st[i]);

@@ -41,10 +41,11 @@ def in_frame_patches(by, bx, W, H):
     return sum(1 for a in range(8) for b in range(8) if by * 16 + 2 * a < H and bx * 16 + 2 * b < W)
 
 
-def compare(frame, mb_lost, gpu, orc, p: skmmse.Params, tol=TOL_FP32, forced=False):
+def compare(frame, mb_lost, gpu, orc, p: skmmse.Params, tol=TOL_FP32, forced=False, near_tie=1.0):
     """gpu/orc: dicts with 'out_f32'/'out' arrays and 'trace'.  Returns a report dict;
     raises AssertionError on a genuine mismatch (or, free-running, an error above tol
-    before the first decision difference of a block)."""
+    before the first decision difference of a block).  near_tie scales the near-tie
+    bounds (free-running mixed precision drifts further from the oracle's inputs)."""
     H, W = frame.shape
     mbh, mbw = mb_lost.shape
     lost = [(y, x) for y in range(mbh) for x in range(mbw) if mb_lost[y, x]]
@@ -85,7 +86,7 @@ def compare(frame, mb_lost, gpu, orc, p: skmmse.Params, tol=TOL_FP32, forced=Fal
             if kind is not None:
                 margin = {"phi": o["margin_phi"], "nu": o["margin_nu"], "beta": o["margin_beta"],
                           "i0": o["margin_i0"]}[kind]
-                assert margin <= NEAR_TIE[kind], (
+                assert margin <= NEAR_TIE[kind] * near_tie, (
                     f"block {b} step {s}: {kind} decision differs with oracle margin {margin:.3g} "
                     f"(gpu layer {int(g['layer'])} ring {int(g['ring'])} beta {int(g['beta_idx'])}, "
                     f"oracle layer {int(o['layer'])} ring {int(o['ring'])} beta {int(o['beta_idx'])})")
@@ -145,3 +146,25 @@ def free_running_summary(frame, mb_lost, gpu, orc):
             "mean_err": float(d.mean()) if d.size else 0.0,
             "psnr_gpu": synth.psnr(gpu["out"], frame, lost),
             "psnr_oracle": synth.psnr(ref_q, frame, lost)}
+
+
+def assembled_psnr_delta(frame, mb_lost, gpu, orc):
+    """|PSNR(gpu) - PSNR(oracle)| over the lost pixels of the frames assembled from the two
+    sets of per-step estimates (trace x, rounded to 8 bits).  With a teacher-forced pair
+    this measures the arithmetic of the path alone: every step had the oracle's inputs."""
+    from paper_2205_11226_gb300 import synth
+    H, W = frame.shape
+    mbh, mbw = mb_lost.shape
+    lost = [(y, x) for y in range(mbh) for x in range(mbw) if mb_lost[y, x]]
+    out = {}
+    for name, tr in (("gpu", gpu["trace"]), ("orc", orc["trace"])):
+        a = np.full((H, W), np.nan)
+        for rank, (by, bx) in enumerate(lost):
+            for s in range(in_frame_patches(by, bx, W, H)):
+                rec = tr[rank, s]
+                pa, pb = int(rec["patch"]) >> 3, int(rec["patch"]) & 7
+                y, x = by * 16 + 2 * pa, bx * 16 + 2 * pb
+                a[y:y + 2, x:x + 2] = np.asarray(rec["x"], np.float64).reshape(2, 2)
+        out[name] = np.clip(np.rint(a), 0, 255)
+    lm = synth.lost_pixel_mask(mb_lost, W, H)
+    return abs(synth.psnr(out["gpu"], frame, lm) - synth.psnr(out["orc"], frame, lm))

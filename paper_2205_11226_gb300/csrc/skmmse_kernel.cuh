@@ -41,6 +41,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kMaxNy = 32;
 constexpr int kCh = 64;          // HQL candidate chunk
 constexpr int kZs = 40;          // staged row: x'(4) y'(32) one(1) pad(3)
+constexpr int kZrow = 44;        // row stride of the staged rows (a lane per row: no bank conflicts)
 constexpr int kMaxBeta = 32;
 constexpr int kMaxI0 = 33;
 constexpr int kNStats = 64;
@@ -193,7 +194,7 @@ struct __align__(16) Hql {
     union {
         df32 accBd[kMaxBeta][kZs];  // beta-pass sums (double-float), end of H3 only
         struct {  // CUDA-core staging and phase buffers
-            __align__(16) float Z[2][kCh][kZs];  // staged candidates, centred by the integer shift
+            __align__(16) float Z[2][kCh][kZrow];  // staged candidates, centred by the integer shift
             union {
                 HqlP1 p1;
                 HqlP2 p2;
@@ -614,20 +615,29 @@ __device__ __forceinline__ void hql_build_koff(Hql& h, int nz) {
     }
 }
 
-// stage candidates [c0, c0+n) into Z[buf]: x' (4), y' (ny), 1, zero padding
+// stage candidates [c0, c0+n) into Z[buf]: x' (4), y' (ny), 1, zero padding.  Thread t
+// fills columns 10 (t & 3) .. +9 of candidate rows t >> 2 (and + 64 when kCh > 64): one
+// candidate offset per row and ten independent loads.
 __device__ __forceinline__ void hql_stage(Smem& sm, int buf, int c0, int n, float shift) {
+    static_assert(kZs == 40 && kThreads == 256 && kCh == 64, "staging layout");
     Hql& h = sm.hql;
-#pragma unroll 2
-    for (int idx = threadIdx.x; idx < kCh * kZs; idx += kThreads) {
-        const int j = idx / kZs, k = idx - j * kZs;
-        const int o = h.koff[k];
-        float v = 0.0f;
-        if (j < n) {
-            if (o >= 0) v = sm.S[h.cand[c0 + j] + o] - shift;
-            else if (o == -2) v = 1.0f;
+    const int j = threadIdx.x >> 2, k0 = 10 * (threadIdx.x & 3);
+    const bool live = j < n;
+    const int cb = live ? h.cand[c0 + j] : 0;
+    float v[10];
+#pragma unroll
+    for (int t = 0; t < 10; ++t) {
+        const int o = h.koff[k0 + t];
+        float x = 0.0f;
+        if (live) {
+            if (o >= 0) x = sm.S[cb + o] - shift;
+            else if (o == -2) x = 1.0f;
         }
-        h.Z[buf][j][k] = v;
+        v[t] = x;
     }
+    float* dst = &h.Z[buf][j][k0];
+#pragma unroll
+    for (int t = 0; t < 10; t += 2) *reinterpret_cast<float2*>(dst + t) = make_float2(v[t], v[t + 1]);
 }
 
 // stage the integer parts (as int) into Z[0] and the fractions into Z[1]; returns whether
@@ -644,8 +654,8 @@ __device__ __forceinline__ bool hql_stage_split(Smem& sm, int c0, int n, float s
         float v = 0.0f;
         if (j < n && o >= 0) v = sm.S[h.cand[c0 + j] + o] - shift;
         const float nv = rintf(v);
-        zi[idx] = __float2int_rn(nv);
-        zf[idx] = v - nv;
+        zi[j * kZrow + k] = __float2int_rn(nv);
+        zf[j * kZrow + k] = v - nv;
         frac = frac || (v != nv);
     }
     return frac;
@@ -653,6 +663,43 @@ __device__ __forceinline__ bool hql_stage_split(Smem& sm, int c0, int n, float s
 
 // whitened coordinates of candidates tj, tj+1 (rows of Z[buf]), coordinates 4tq..4tq+3:
 // u = L^-1 (y_j - y0)
+// whitened coordinates 4q..4q+3 (ua) and 4(7-q)..4(7-q)+3 (ub) of candidate j (row j of
+// Z[buf]).  L^-1 is lower triangular, so the two groups take q+1 and 8-q steps: 9 for every
+// q.  Callers give all lanes of a warp the same q (no divergence) and one candidate each.
+__device__ __forceinline__ void whiten_quads(const Hql& h, int buf, int ny, int j, int q,
+                                             float ua[4], float ub[4]) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        ua[r] = 0.0f;
+        ub[r] = 0.0f;
+    }
+    const int qb = 7 - q;
+    for (int l4 = 0; l4 <= qb; ++l4) {
+        if (4 * l4 >= ny) break;
+        const float4 ev = *reinterpret_cast<const float4*>(&h.Z[buf][j][4 + 4 * l4]);
+        const float4 ysv = *reinterpret_cast<const float4*>(&h.ys[4 * l4]);
+        const float e[4] = {ev.x - ysv.x, ev.y - ysv.y, ev.z - ysv.z, ev.w - ysv.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float4 lv = *reinterpret_cast<const float4*>(&h.Linv[4 * qb + r][4 * l4]);
+            ub[r] = __fmaf_rn(lv.x, e[0], ub[r]);
+            ub[r] = __fmaf_rn(lv.y, e[1], ub[r]);
+            ub[r] = __fmaf_rn(lv.z, e[2], ub[r]);
+            ub[r] = __fmaf_rn(lv.w, e[3], ub[r]);
+        }
+        if (l4 <= q) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float4 lv = *reinterpret_cast<const float4*>(&h.Linv[4 * q + r][4 * l4]);
+                ua[r] = __fmaf_rn(lv.x, e[0], ua[r]);
+                ua[r] = __fmaf_rn(lv.y, e[1], ua[r]);
+                ua[r] = __fmaf_rn(lv.z, e[2], ua[r]);
+                ua[r] = __fmaf_rn(lv.w, e[3], ua[r]);
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ void whiten_tile(const Hql& h, int buf, int ny, int tj, int tq,
                                             float u0[4], float u1[4]) {
 #pragma unroll
@@ -1076,13 +1123,13 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
             const bool any_frac = __syncthreads_or(frac) != 0;
             if (act) {
                 for (int j = g; j < n; j += kG1) {
-                    const int na = zi[j * kZs + a];
-                    const float fa = zf[j * kZs + a];
+                    const int na = zi[j * kZrow + a];
+                    const float fa = zf[j * kZrow + a];
                     colN += na;
                     colF += fa;
 #pragma unroll
                     for (int b4 = 0; b4 < 9; ++b4) {
-                        const int4 nb = *reinterpret_cast<const int4*>(&zi[j * kZs + 4 * b4]);
+                        const int4 nb = *reinterpret_cast<const int4*>(&zi[j * kZrow + 4 * b4]);
                         ai[4 * b4 + 0] += na * nb.x;
                         ai[4 * b4 + 1] += na * nb.y;
                         ai[4 * b4 + 2] += na * nb.z;
@@ -1092,8 +1139,8 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
                         const float naf = (float)na;
 #pragma unroll
                         for (int b4 = 0; b4 < 9; ++b4) {
-                            const int4 nb = *reinterpret_cast<const int4*>(&zi[j * kZs + 4 * b4]);
-                            const float4 fb = *reinterpret_cast<const float4*>(&zf[j * kZs + 4 * b4]);
+                            const int4 nb = *reinterpret_cast<const int4*>(&zi[j * kZrow + 4 * b4]);
+                            const float4 fb = *reinterpret_cast<const float4*>(&zf[j * kZrow + 4 * b4]);
                             // n_a f_b + f_a (n_b + f_b)
                             af[4 * b4 + 0] = __fmaf_rn(naf, fb.x, __fmaf_rn(fa, (float)nb.x + fb.x, af[4 * b4 + 0]));
                             af[4 * b4 + 1] = __fmaf_rn(naf, fb.y, __fmaf_rn(fa, (float)nb.y + fb.y, af[4 * b4 + 1]));
@@ -1506,23 +1553,16 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
         for (int ch = 0; ch < nchunks; ++ch) {
             const int buf = ch & 1, c0 = ch * kCh, n = min(kCh, M - c0);
             __syncthreads();  // staged chunk visible; previous chunk's Vs / Wt consumed
-            {
-                float u0[4], u1[4];
-                whiten_tile(h, buf, ny, tj, tq, u0, u1);
-                *reinterpret_cast<float4*>(&h.p2.Vs[tj][4 + 4 * tq]) = make_float4(u0[0], u0[1], u0[2], u0[3]);
-                *reinterpret_cast<float4*>(&h.p2.Vs[tj + 1][4 + 4 * tq]) = make_float4(u1[0], u1[1], u1[2], u1[3]);
-                if (tq == 0) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        h.p2.Vs[tj][q] = h.Z[buf][tj][q];
-                        h.p2.Vs[tj + 1][q] = h.Z[buf][tj + 1][q];
-                    }
-                } else if (tq == 1) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        h.p2.Vs[tj][36 + q] = q == 0 ? h.Z[buf][tj][36] : 0.0f;
-                        h.p2.Vs[tj + 1][36 + q] = q == 0 ? h.Z[buf][tj + 1][36] : 0.0f;
-                    }
+            {   // warp w: coordinate groups (w & 3, 7 - (w & 3)) of candidates 32 (w >> 2) + lane
+                const int qw = wid & 3, jw = lane + 32 * (wid >> 2);
+                float ua[4], ub[4];
+                whiten_quads(h, buf, ny, jw, qw, ua, ub);
+                *reinterpret_cast<float4*>(&h.p2.Vs[jw][4 + 4 * qw]) = make_float4(ua[0], ua[1], ua[2], ua[3]);
+                *reinterpret_cast<float4*>(&h.p2.Vs[jw][4 + 4 * (7 - qw)]) = make_float4(ub[0], ub[1], ub[2], ub[3]);
+                if (qw == 0) {
+                    *reinterpret_cast<float4*>(&h.p2.Vs[jw][0]) = *reinterpret_cast<const float4*>(&h.Z[buf][jw][0]);
+                } else if (qw == 1) {
+                    *reinterpret_cast<float4*>(&h.p2.Vs[jw][36]) = make_float4(h.Z[buf][jw][36], 0.0f, 0.0f, 0.0f);
                 }
             }
             __syncthreads();
@@ -1553,28 +1593,34 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
                             t = ua[a].w - vb[r].w; d[a][r] = __fmaf_rn(t, t, d[a][r]);
                         }
                 }
+                // the three members side by side: independent shuffle and exp chains
+                float sc[3][4], mx[3], mold[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    float sc[4];
-                    float mx = -INFINITY;
+                    mx[a] = -INFINITY;
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
                         const int j = jq + 16 * r;
                         const bool ok = j < n && c0 + j != selfc[a] && selfc[a] != -2;
-                        sc[r] = ok ? -d[a][r] * ib : -INFINITY;
-                        mx = fmaxf(mx, sc[r]);
+                        sc[a][r] = ok ? -d[a][r] * ib : -INFINITY;
+                        mx[a] = fmaxf(mx[a], sc[a][r]);
                     }
+                    mold[a] = h.p2.mrow[3 * it + a];
+                }
 #pragma unroll
-                    for (int o = 8; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+                __syncwarp();  // every lane has read the old maxima
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
                     const int i = 3 * it + a;
-                    const float mold = h.p2.mrow[i];
-                    const float mnew = fmaxf(mold, mx);
+                    const float mnew = fmaxf(mold[a], mx[a]);
 #pragma unroll
                     for (int r = 0; r < 4; ++r)
-                        h.p2.Wt[jq + 16 * r][i] = sc[r] == -INFINITY ? 0.0f : expf(sc[r] - mnew);
-                    __syncwarp();
+                        h.p2.Wt[jq + 16 * r][i] = sc[a][r] == -INFINITY ? 0.0f : expf(sc[a][r] - mnew);
                     if (jq == 0) {
-                        h.p2.scl[i] = mold == -INFINITY ? 0.0f : expf(mold - mnew);
+                        h.p2.scl[i] = mold[a] == -INFINITY ? 0.0f : expf(mold[a] - mnew);
                         h.p2.mrow[i] = mnew;
                     }
                 }

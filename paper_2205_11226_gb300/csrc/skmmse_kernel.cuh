@@ -157,7 +157,7 @@ struct __align__(16) HqlP2 {                 // beta / leave-one-out phase
             __align__(16) float Wt[kCh][kI0Pad];   // leave-one-out weights, candidate-major
         };
         float mrg[kThreads][37];             // per-thread partial sums before a merge
-        float accP[2][kI0Pad][40];           // leave-one-out sums of the two candidate halves
+        float accP[4][kI0Pad][40];           // leave-one-out sums of the candidate groups
     };
     float mrow[kI0Pad];                      // running maximum score per member
     float scl[kI0Pad];                       // rescaling of the member's sums for this chunk
@@ -501,7 +501,7 @@ struct IdlOut {
     int r;      // 1 accepted, 0 not accepted, -1 no candidate
 };
 
-__device__ __noinline__ IdlOut idl_step(const KParams& P, int wr, int wc,
+__device__ __forceinline__ IdlOut idl_step(const KParams& P, int wr, int wc,
                                         unsigned long long ymask, int ny, float mean) {
     Smem& sm = smem_ref();
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -874,9 +874,10 @@ __device__ __noinline__ void h1_mixed(int M, float shift, uint32_t tmem, uint32_
     zero_tiles(h);
     __syncthreads();
     const int arow = 32 * wid + lane;  // warps 0, 1: the row of D this thread reads
-    int ni[37];
-#pragma unroll
-    for (int b = 0; b < 37; ++b) ni[b] = 0;
+    // integer sums: the thread's own row of an int32 array in tile t3 (unused by this pass,
+    // cleared above; p1 shares storage with the live tiles t1, t2)
+    int(*nacc)[40] = reinterpret_cast<int(*)[40]>(h.mx.t3);
+    static_assert(sizeof(h.mx.t3) >= 36 * 40 * sizeof(int), "integer sums fit tile t3");
     for (int ch = 0; ch < nchunks; ++ch) {
         const int c0 = ch * kCh, n = min(kCh, M - c0);
         stage_zt<BF16, true>(sm, c0, n, shift);
@@ -897,30 +898,38 @@ __device__ __noinline__ void h1_mixed(int M, float shift, uint32_t tmem, uint32_
             }
         });
         if (wid < 2 && ((ch & 3) == 3 || ch == nchunks - 1)) {  // exact sums into int32
-            float D[48];
+            for (int c = 0; c < 5; ++c) {  // columns 0..39 in groups of 8 (36: column sums)
+                float D[8];
+                tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 8 * c, D);
+                if (arow < 36) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 8 * c, &D[8 * c]);
-#pragma unroll
-            for (int b = 0; b < 37; ++b) ni[b] += __float2int_rn(D[b]);
+                    for (int t = 0; t < 8; ++t) nacc[arow][8 * c + t] += __float2int_rn(D[t]);
+                }
+            }
         }
         // (the next chunk's mma_round orders these tensor-memory reads before its MMAs)
     }
-    float F[48];
+    // every MMA has completed: the operand tiles are dead and p1 may take the sums
     if (wid < 2) {
+        for (int c = 0; c < 5; ++c) {
+            float F[8];
+            tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 64 + 8 * c, F);
+            if (arow < 36) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 64 + 8 * c, &F[8 * c]);
+                for (int t = 0; t < 8; ++t) {
+                    const int b = 8 * c + t;
+                    if (b < 36) {
+                        h.p1.cfrac[arow][b] = F[t];
+                        h.p1.cint[arow][b] = nacc[arow][b];
+                    } else if (b == 36) {
+                        h.colF[arow] = F[t];
+                        h.colNi[arow] = nacc[arow][36];
+                    }
+                }
+            }
+        }
     }
     tc::fence_before();
-    __syncthreads();  // the tiles are dead: their storage takes the sums
-    if (wid < 2 && arow < 36) {
-#pragma unroll
-        for (int b = 0; b < 36; ++b) {
-            h.p1.cint[arow][b] = ni[b];
-            h.p1.cfrac[arow][b] = F[b];
-        }
-        h.colNi[arow] = ni[36];
-        h.colF[arow] = F[36];
-    }
     __syncthreads();
 }
 
@@ -959,13 +968,14 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
         }
         mma_round(sm, mph, [&]() { mma3(tmem, h.mx.t0, h.mx.t1, h.mx.t2, h.mx.t3, 32, tc::idesc_f16(128, 32, BF16), false); });
         if (wid < 2) {
-            float u[32];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 8 * c, &u[8 * c]);
             const int j = 32 * wid + lane;
             float dd = 0.0f;
+            for (int c = 0; c < 4; ++c) {  // groups of 8 columns (few live registers)
+                float u[8];
+                tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 8 * c, u);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) dd = __fmaf_rn(u[k], u[k], dd);
+                for (int k = 0; k < 8; ++k) dd = __fmaf_rn(u[k], u[k], dd);
+            }
             if (j < n) {
                 h.d[c0 + j] = dd;
                 lmin = fminf(lmin, dd);
@@ -1009,16 +1019,87 @@ __device__ __noinline__ void h3_mixed(const KParams& P, int M, float shift, floa
         mma_round(sm, mph, [&]() { mma3(tmem, h.mx.t2, h.mx.t3, h.mx.t0, h.mx.t1, 64, tc::idesc_f16(128, 48, BF16), ch > 0); });
     }
     if (wid == 0) {
-        float D[48];
+        for (int c = 0; c < 5; ++c) {  // columns 0..39 in groups of 8
+            float D[8];
+            tc::tmem_ld8(tmem + 8 * c, D);
+            if (lane < nb) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) tc::tmem_ld8(tmem + 8 * c, &D[8 * c]);
-        if (lane < nb) {
-#pragma unroll
-            for (int k = 0; k < 37; ++k) h.accBd[lane][k] = df_make(D[k]);
+                for (int t = 0; t < 8; ++t)
+                    if (8 * c + t < 37) h.accBd[lane][8 * c + t] = df_make(D[t]);
+            }
         }
     }
     tc::fence_before();
     __syncthreads();
+}
+
+// Leave-one-out scores of one chunk (H5): thread (it, jq) owns members 3it..3it+2 against
+// candidates jq + L r (r < 64 / L), with L lanes per member triple (L = 16 or 32: fewer
+// candidates per thread when n0 is small).  Squared whitened distances, the chunk maximum
+// per member (shuffles over the L lanes), the new running maximum and the weights.
+template <int L>
+__device__ __forceinline__ void h5_scores(Hql& h, int n0, int nyq, int n, int c0, float ib) {
+    constexpr int R = 64 / L;
+    const int tid = threadIdx.x;
+    const int it = tid / L, jq = tid % L;
+    if (3 * it >= n0) return;  // (whole lane groups: L divides 32 or equals it)
+    int selfc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) selfc[a] = 3 * it + a < n0 ? h.i0[3 * it + a] : -2;
+    float d[3][R];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[a][r] = 0.0f;
+    for (int l4 = 0; l4 < nyq; ++l4) {
+        float4 ua[3], vb[R];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ua[a] = *reinterpret_cast<const float4*>(&h.UI[3 * it + a][4 * l4]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) vb[r] = *reinterpret_cast<const float4*>(&h.p2.Vs[jq + L * r][4 + 4 * l4]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float t;
+                t = ua[a].x - vb[r].x; d[a][r] = __fmaf_rn(t, t, d[a][r]);
+                t = ua[a].y - vb[r].y; d[a][r] = __fmaf_rn(t, t, d[a][r]);
+                t = ua[a].z - vb[r].z; d[a][r] = __fmaf_rn(t, t, d[a][r]);
+                t = ua[a].w - vb[r].w; d[a][r] = __fmaf_rn(t, t, d[a][r]);
+            }
+    }
+    // the three members side by side: independent shuffle and exp chains
+    float sc[3][R], mx[3], mold[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        mx[a] = -INFINITY;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int j = jq + L * r;
+            const bool ok = j < n && c0 + j != selfc[a] && selfc[a] != -2;
+            sc[a][r] = ok ? -d[a][r] * ib : -INFINITY;
+            mx[a] = fmaxf(mx[a], sc[a][r]);
+        }
+        mold[a] = h.p2.mrow[3 * it + a];
+    }
+    const unsigned gmask = L == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) mx[a] = fmaxf(mx[a], __shfl_xor_sync(gmask, mx[a], o));
+    __syncwarp(gmask);  // every lane of the group has read the old maxima
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int i = 3 * it + a;
+        const float mnew = fmaxf(mold[a], mx[a]);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            h.p2.Wt[jq + L * r][i] = sc[a][r] == -INFINITY ? 0.0f : expf(sc[a][r] - mnew);
+        if (jq == 0) {
+            h.p2.scl[i] = mold[a] == -INFINITY ? 0.0f : expf(mold[a] - mnew);
+            h.p2.mrow[i] = mnew;
+        }
+    }
 }
 
 // Not inlined: HQL runs for a small share of the patches, and as a function of its own its
@@ -1526,19 +1607,13 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
     if (n0 > 0) {
         const float ib = P.inv2beta[bstar];
         const int nyq = (ny + 3) >> 2;
-        // scores: thread (it, jq) owns members 3it..3it+2 x candidates jq + 16r (r < 4)
-        const int it = tid >> 4, jq = tid & 15;
-        const bool sc_act = it < kI0Pad / 3;
-        int selfc[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int i = 3 * it + a;
-            selfc[a] = (sc_act && i < n0) ? h.i0[i] : -2;  // -2: padding member (masked)
-        }
+        const int ntrip = (n0 + 2) / 3;  // member triples with a real member
         // sums: thread (ib4, kb, jg) owns members 4ib4..+3 x columns 4kb..+3 over candidates
-        // jg, jg + 2, ... of each chunk
-        const int jg = tid / 90, rr = tid - jg * 90, ib4 = rr / 10, kb = rr - ib4 * 10;
-        const bool ac_act = tid < 180;
+        // jg, jg + G, ... of each chunk; G candidate groups, as many as the threads allow
+        const int tasks = ((n0 + 3) / 4) * 10;
+        const int G = min(4, kThreads / tasks);
+        const int jg = tid / tasks, rr = tid - jg * tasks, ib4 = rr / 10, kb = rr - ib4 * 10;
+        const bool ac_act = jg < G;
         float acc[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -1570,61 +1645,8 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
             if (ch + 1 < nchunks) hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), shift);
             // squared whitened distances, scores, chunk maxima and weights (Eq. (12) with
             // candidate i left out)
-            if (sc_act) {
-                float d[3][4];
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) d[a][r] = 0.0f;
-                for (int l4 = 0; l4 < nyq; ++l4) {
-                    float4 ua[3], vb[4];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) ua[a] = *reinterpret_cast<const float4*>(&h.UI[3 * it + a][4 * l4]);
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) vb[r] = *reinterpret_cast<const float4*>(&h.p2.Vs[jq + 16 * r][4 + 4 * l4]);
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            float t;
-                            t = ua[a].x - vb[r].x; d[a][r] = __fmaf_rn(t, t, d[a][r]);
-                            t = ua[a].y - vb[r].y; d[a][r] = __fmaf_rn(t, t, d[a][r]);
-                            t = ua[a].z - vb[r].z; d[a][r] = __fmaf_rn(t, t, d[a][r]);
-                            t = ua[a].w - vb[r].w; d[a][r] = __fmaf_rn(t, t, d[a][r]);
-                        }
-                }
-                // the three members side by side: independent shuffle and exp chains
-                float sc[3][4], mx[3], mold[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    mx[a] = -INFINITY;
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const int j = jq + 16 * r;
-                        const bool ok = j < n && c0 + j != selfc[a] && selfc[a] != -2;
-                        sc[a][r] = ok ? -d[a][r] * ib : -INFINITY;
-                        mx[a] = fmaxf(mx[a], sc[a][r]);
-                    }
-                    mold[a] = h.p2.mrow[3 * it + a];
-                }
-#pragma unroll
-                for (int o = 8; o > 0; o >>= 1)
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
-                __syncwarp();  // every lane has read the old maxima
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const int i = 3 * it + a;
-                    const float mnew = fmaxf(mold[a], mx[a]);
-#pragma unroll
-                    for (int r = 0; r < 4; ++r)
-                        h.p2.Wt[jq + 16 * r][i] = sc[a][r] == -INFINITY ? 0.0f : expf(sc[a][r] - mnew);
-                    if (jq == 0) {
-                        h.p2.scl[i] = mold[a] == -INFINITY ? 0.0f : expf(mold[a] - mnew);
-                        h.p2.mrow[i] = mnew;
-                    }
-                }
-            }
+            if (ntrip <= 8) h5_scores<32>(h, n0, nyq, n, c0, ib);
+            else h5_scores<16>(h, n0, nyq, n, c0, ib);
             __syncthreads();
             SK_PHASE(PH_X2);
             // weighted sums of [x' | u | 1] (online, rescaled by the new maxima)
@@ -1635,7 +1657,7 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) acc[a][q] *= sv[a];
-                for (int j = jg; j < n; j += 2) {
+                for (int j = jg; j < n; j += G) {
                     const float4 w4 = *reinterpret_cast<const float4*>(&h.p2.Wt[j][4 * ib4]);
                     const float4 v4 = *reinterpret_cast<const float4*>(&h.p2.Vs[j][4 * kb]);
                     const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
@@ -1657,7 +1679,9 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
         __syncthreads();
         for (int idx = tid; idx < n0 * 37; idx += kThreads) {
             const int i = idx / 37, k = idx - (idx / 37) * 37;
-            h.accI[i][k] = h.p2.accP[0][i][k] + h.p2.accP[1][i][k];
+            float a = h.p2.accP[0][i][k];
+            for (int g = 1; g < G; ++g) a += h.p2.accP[g][i][k];
+            h.accI[i][k] = a;
         }
         __syncthreads();
         // r_i = x_i - x~_i ; g_i = G (u_i - u~_i) ; alpha = sum r.g / sum g.g

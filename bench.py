@@ -567,29 +567,41 @@ def forced_agreement(ctx, skmmse, p, frames_masks):
 
 def run_serve(args):
     """Serving stream (Poisson arrivals at 600 frames/s, sizes 1/3 each of 352x288,
-    1280x720, 1920x1080, loss U[2, 30] %): p50/p99 latency and sustained blocks/s."""
+    1280x720, 1920x1080, loss U[2, 30] %): p50/p99 latency and sustained blocks/s, at
+    --precision and in FP32 on the same request stream."""
     import torch
     from paper_2205_11226_gb300 import build as skbuild
     skbuild.build()
     from paper_2205_11226_gb300 import serving, skmmse
     torch.cuda.set_device(0)
     reqs = serving.make_requests(args.serve_requests, seed=args.seed)
-    warm = serving.make_requests(64, seed=args.seed + 99, rate_hz=5000.0)
-    loop = serving.ServeLoop(skmmse.params(args.profile), n_streams=3)
-    loop.run(warm, realtime=True)
-    loop.max_overlap = 0
-    loop.n_batches = 0
-    with ClockSampler(0) as clk:
-        res = loop.run(reqs, realtime=True)
-    loop.close()
+    results = {}
+    clocks = None
+    for name in dict.fromkeys([args.precision, "fp32"]):
+        p = skmmse.params(args.profile, precision=PRECISIONS[name])
+        warm = serving.make_requests(64, seed=args.seed + 99, rate_hz=5000.0)
+        loop = serving.ServeLoop(p, n_streams=3)
+        loop.run(warm, realtime=True)
+        loop.max_overlap = 0
+        loop.n_batches = 0
+        for r in reqs:
+            r.t_done, r.result = None, None
+        with ClockSampler(0) as clk:
+            results[name] = loop.run(reqs, realtime=True)
+        if clocks is None:
+            clocks = clk.summary()
+        loop.close()
+    res = results[args.precision]
     line = {"metric": "served 16x16 MBs/s (Poisson 600 frames/s stream)", "value": res["mbs_per_s"],
-            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": DTYPES[args.precision],
             "data": "synthetic stream (seeded frames from a pool per size, per-request loss maps)",
             "config": {"workload": f"serve_{args.serve_requests}_requests_600hz", "profile": args.profile,
-                       "streams": 3, "budget_bytes": 2 << 30},
+                       "precision": args.precision, "streams": 3, "budget_bytes": 2 << 30},
             "p50_ms": res["p50_ms"], "p99_ms": res["p99_ms"], "mean_ms": res["mean_ms"],
             "requests": res["requests"], "batches": res["batches"], "max_overlap": res["max_overlap"],
-            "wall_s": res["wall_s"], "clocks": clk.summary()}
+            "wall_s": res["wall_s"], "clocks": clocks,
+            "fp32": {k: results["fp32"][k] for k in ("mbs_per_s", "p50_ms", "p99_ms", "mean_ms", "batches",
+                                                      "max_overlap")}}
     print(json.dumps(line), flush=True)
 
 

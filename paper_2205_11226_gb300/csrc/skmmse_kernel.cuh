@@ -458,20 +458,22 @@ struct CtxStats {
 // context of the window at (wr, wc): size, flatness and mean.  Warp-level reductions; every
 // lane returns the same values.
 __device__ __forceinline__ CtxStats ctx_stats(const Smem& sm, int wr, int wc, int lane) {
-    unsigned long long ymask = 0;
-#pragma unroll
-    for (int r = 0; r < 6; ++r) ymask |= (unsigned long long)((sm.av[wr + r] >> wc) & 63ull) << (6 * r);
     float mx = -INFINITY, mn = INFINITY, sum = 0.0f;
+    unsigned bal[2];
 #pragma unroll
-    for (int h2 = 0; h2 < 2; ++h2) {
+    for (int h2 = 0; h2 < 2; ++h2) {  // window position k of this lane: its availability bit
         const int k = lane + 32 * h2;
-        if (k < 36 && ((ymask >> k) & 1ull)) {
-            const float v = sm.S[(wr + k / 6) * kReg + wc + k % 6];
+        const int r = k / 6, c = k - 6 * (k / 6);
+        const bool on = k < 36 && ((sm.av[wr + r] >> (wc + c)) & 1ull);
+        bal[h2] = __ballot_sync(0xffffffffu, on);
+        if (on) {
+            const float v = sm.S[(wr + r) * kReg + wc + c];
             mx = fmaxf(mx, v);
             mn = fminf(mn, v);
             sum += v;
         }
     }
+    const unsigned long long ymask = (unsigned long long)bal[0] | ((unsigned long long)bal[1] << 32);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -831,13 +833,18 @@ __device__ __forceinline__ void mma_round(Smem& sm, uint32_t& mph, IssueF issue)
 // stage rows 0..36 of Z^T for candidates [c0, c0+n): z' (feature rows 0..35, zero beyond
 // nz) and the constant one (row 36)
 template <bool BF16, bool INTFRAC>
-__device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, float shift) {
+__device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, int nz, float shift) {
     Hql& h = sm.hql;
-    // a quarter-warp writes one 16-byte column group of 8 consecutive rows: one 128-byte
-    // core matrix, free of bank conflicts
-    for (int idx = threadIdx.x; idx < 40 * 8; idx += kThreads) {
-        const int a = ((idx >> 6) << 3) | (idx & 7), g8 = (idx >> 3) & 7;
-        if (a > 36) continue;
+    // live rows: the nz = 4 + Ny features and the constant (row 36); the other rows stay
+    // at the zeros the pass started from.  Row slot ri < nz is feature ri, slot nz the
+    // constant.  A quarter-warp writes one 16-byte column group of 8 consecutive slots
+    // (one 128-byte core matrix: no bank conflicts); one task per thread for nz <= 31.
+    const int nr = nz + 1;
+    const int ntask = ((nr + 7) >> 3) * 64;
+    for (int idx = threadIdx.x; idx < ntask; idx += kThreads) {
+        const int ri = ((idx >> 6) << 3) | (idx & 7), g8 = (idx >> 3) & 7;
+        if (ri >= nr) continue;
+        const int a = ri < nz ? ri : 36;
         const int ka = a < kZs ? h.koff[a] : -1;
         float v[8];
 #pragma unroll
@@ -864,7 +871,7 @@ __device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, float shift) {
 // (tensor memory columns 64..111).  The same integer / fraction split as the CUDA-core
 // path, so the covariance keeps its precision through the cancellation in Eq. (8).
 template <bool BF16>
-__device__ __noinline__ void h1_mixed(int M, float shift, uint32_t tmem, uint32_t mph) {
+__device__ __noinline__ void h1_mixed(int M, int nz, float shift, uint32_t tmem, uint32_t mph) {
     Smem& sm = smem_ref();
     Hql& h = sm.hql;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -880,7 +887,7 @@ __device__ __noinline__ void h1_mixed(int M, float shift, uint32_t tmem, uint32_
     static_assert(sizeof(h.mx.t3) >= 36 * 40 * sizeof(int), "integer sums fit tile t3");
     for (int ch = 0; ch < nchunks; ++ch) {
         const int c0 = ch * kCh, n = min(kCh, M - c0);
-        stage_zt<BF16, true>(sm, c0, n, shift);
+        stage_zt<BF16, true>(sm, c0, n, nz, shift);
         mma_round(sm, mph, [&]() {
             const uint32_t sbo = (64 / 8) * 128;
             const uint32_t an = tc::smem_addr(h.mx.t0), ah = tc::smem_addr(h.mx.t1),
@@ -989,7 +996,7 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
 
 // H3 on tensor cores: D[b][k] = sum_j w_j(b) z'_j[k] with w_j(b) = exp(-(d_j - dmin)/(2 beta_b))
 template <bool BF16>
-__device__ __noinline__ void h3_mixed(const KParams& P, int M, float shift, float dmin,
+__device__ __noinline__ void h3_mixed(const KParams& P, int M, int nz, float shift, float dmin,
                                          uint32_t tmem, uint32_t mph) {
     Smem& sm = smem_ref();
     Hql& h = sm.hql;
@@ -1001,7 +1008,7 @@ __device__ __noinline__ void h3_mixed(const KParams& P, int M, float shift, floa
     __syncthreads();
     for (int ch = 0; ch < nchunks; ++ch) {
         const int c0 = ch * kCh, n = min(kCh, M - c0);
-        stage_zt<BF16, false>(sm, c0, n, shift);
+        stage_zt<BF16, false>(sm, c0, n, nz, shift);
         {  // A = W (rows: beta, columns: candidates), one task per thread; a quarter-warp
            // stores 8 consecutive rows of one column group (conflict-free)
             const int b = (tid & 7) | ((tid >> 6) << 3), g8 = (tid >> 3) & 7;
@@ -1167,10 +1174,10 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
     SK_PHASE(PH_H0);
 
     if (MIXED == 1) {
-        h1_mixed<true>(M, shift, sm.tmem_base, mph);
+        h1_mixed<true>(M, nz, shift, sm.tmem_base, mph);
         mph ^= (uint32_t)(nchunks & 1);
     } else if (MIXED == 2) {
-        h1_mixed<false>(M, shift, sm.tmem_base, mph);
+        h1_mixed<false>(M, nz, shift, sm.tmem_base, mph);
         mph ^= (uint32_t)(nchunks & 1);
     } else
     // H1: sums of z' and z' z'^T, z' = z - shift (Eq. (8)).  Thread (a, g) owns row a of the
@@ -1413,10 +1420,10 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
     // Subset partial sums merge in double-float.
     const int nb = P.nbeta;
     if (MIXED == 1) {
-        h3_mixed<true>(P, M, shift, dmin, sm.tmem_base, mph);
+        h3_mixed<true>(P, M, nz, shift, dmin, sm.tmem_base, mph);
         mph ^= (uint32_t)(nchunks & 1);
     } else if (MIXED == 2) {
-        h3_mixed<false>(P, M, shift, dmin, sm.tmem_base, mph);
+        h3_mixed<false>(P, M, nz, shift, dmin, sm.tmem_base, mph);
         mph ^= (uint32_t)(nchunks & 1);
     } else {
         const int G3 = kThreads / nb;

@@ -152,15 +152,15 @@ constexpr int kI0Pad = 36;   // leave-one-out members padded to whole 3-member t
 constexpr int kVs = 44;      // row stride of a whitened chunk (conflict-free 16-byte reads)
 struct __align__(16) HqlP2 {                 // beta / leave-one-out phase
     union {
-        struct {
-            __align__(16) float Vs[kCh][kVs];      // whitened chunk: x'(4) u(32) 1 pad
-            __align__(16) float Wt[kCh][kI0Pad];   // leave-one-out weights, candidate-major
+        struct {  // two buffers: chunk c is whitened while chunk c-1 is summed
+            __align__(16) float Vs[2][kCh][kVs];      // whitened chunk: x'(4) u(32) 1 pad
+            __align__(16) float Wt[2][kCh][kI0Pad];   // leave-one-out weights, candidate-major
         };
         float mrg[kThreads][37];             // per-thread partial sums before a merge
         float accP[4][kI0Pad][40];           // leave-one-out sums of the candidate groups
     };
     float mrow[kI0Pad];                      // running maximum score per member
-    float scl[kI0Pad];                       // rescaling of the member's sums for this chunk
+    float scl[2][kI0Pad];                    // rescaling of the member's sums for a chunk
 };
 
 struct __align__(16) Hql {
@@ -1045,7 +1045,7 @@ __device__ __noinline__ void h3_mixed(const KParams& P, int M, int nz, float shi
 // candidates per thread when n0 is small).  Squared whitened distances, the chunk maximum
 // per member (shuffles over the L lanes), the new running maximum and the weights.
 template <int L>
-__device__ __forceinline__ void h5_scores(Hql& h, int n0, int nyq, int n, int c0, float ib) {
+__device__ __forceinline__ void h5_scores(Hql& h, int vb_, int n0, int nyq, int n, int c0, float ib) {
     constexpr int R = 64 / L;
     const int tid = threadIdx.x;
     const int it = tid / L, jq = tid % L;
@@ -1063,7 +1063,7 @@ __device__ __forceinline__ void h5_scores(Hql& h, int n0, int nyq, int n, int c0
 #pragma unroll
         for (int a = 0; a < 3; ++a) ua[a] = *reinterpret_cast<const float4*>(&h.UI[3 * it + a][4 * l4]);
 #pragma unroll
-        for (int r = 0; r < R; ++r) vb[r] = *reinterpret_cast<const float4*>(&h.p2.Vs[jq + L * r][4 + 4 * l4]);
+        for (int r = 0; r < R; ++r) vb[r] = *reinterpret_cast<const float4*>(&h.p2.Vs[vb_][jq + L * r][4 + 4 * l4]);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -1101,9 +1101,9 @@ __device__ __forceinline__ void h5_scores(Hql& h, int n0, int nyq, int n, int c0
         const float mnew = fmaxf(mold[a], mx[a]);
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            h.p2.Wt[jq + L * r][i] = sc[a][r] == -INFINITY ? 0.0f : expf(sc[a][r] - mnew);
+            h.p2.Wt[vb_][jq + L * r][i] = sc[a][r] == -INFINITY ? 0.0f : expf(sc[a][r] - mnew);
         if (jq == 0) {
-            h.p2.scl[i] = mold[a] == -INFINITY ? 0.0f : expf(mold[a] - mnew);
+            h.p2.scl[vb_][i] = mold[a] == -INFINITY ? 0.0f : expf(mold[a] - mnew);
             h.p2.mrow[i] = mnew;
         }
     }
@@ -1427,6 +1427,7 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
         mph ^= (uint32_t)(nchunks & 1);
     } else {
         const int G3 = kThreads / nb;
+        const int kql3 = (nz + 3) / 4;  // live column quads: 0 .. nz-1, and the constant (9)
         const int b = tid % nb, g = tid / nb;
         const bool act = g < G3;
         const float ib = P.inv2beta[b];
@@ -1442,6 +1443,7 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
                     const float w = expf(-(h.d[c0 + j] - dmin) * ib);
 #pragma unroll
                     for (int k4 = 0; k4 < kZs / 4; ++k4) {
+                        if (k4 >= kql3 && k4 != 9) continue;  // columns past the context are zero
                         const float4 z = *reinterpret_cast<const float4*>(&h.Z[buf][j][4 * k4]);
                         acc[4 * k4 + 0] = __fmaf_rn(w, z.x, acc[4 * k4 + 0]);
                         acc[4 * k4 + 1] = __fmaf_rn(w, z.y, acc[4 * k4 + 1]);
@@ -1617,9 +1619,12 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
         const int ntrip = (n0 + 2) / 3;  // member triples with a real member
         // sums: thread (ib4, kb, jg) owns members 4ib4..+3 x columns 4kb..+3 over candidates
         // jg, jg + G, ... of each chunk; G candidate groups, as many as the threads allow
-        const int tasks = ((n0 + 3) / 4) * 10;
+        // live column quads of [x' | u | 1]: columns 0 .. 3 + ny, and the constant (quad 9)
+        const int kql = (4 + ny + 3) / 4, nkq = kql + (kql <= 9 ? 1 : 0);
+        const int tasks = ((n0 + 3) / 4) * nkq;
         const int G = min(4, kThreads / tasks);
-        const int jg = tid / tasks, rr = tid - jg * tasks, ib4 = rr / 10, kb = rr - ib4 * 10;
+        const int jg = tid / tasks, rr = tid - jg * tasks, ib4 = rr / nkq, kq = rr - ib4 * nkq;
+        const int kb = kq < kql ? kq : 9;
         const bool ac_act = jg < G;
         float acc[4][4];
 #pragma unroll
@@ -1632,41 +1637,22 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
                 for (int k = 0; k < 36; ++k) h.UI[tid][k] = 0.0f;
         }
         hql_stage(sm, 0, 0, min(kCh, M), shift);
-        for (int ch = 0; ch < nchunks; ++ch) {
+        // chunk c: [barrier] sums of chunk c-1 and whitening of chunk c [barrier] staging of
+        // chunk c+1 and the scores of chunk c
+        for (int ch = 0; ch <= nchunks; ++ch) {
             const int buf = ch & 1, c0 = ch * kCh, n = min(kCh, M - c0);
-            __syncthreads();  // staged chunk visible; previous chunk's Vs / Wt consumed
-            {   // warp w: coordinate groups (w & 3, 7 - (w & 3)) of candidates 32 (w >> 2) + lane
-                const int qw = wid & 3, jw = lane + 32 * (wid >> 2);
-                float ua[4], ub[4];
-                whiten_quads(h, buf, ny, jw, qw, ua, ub);
-                *reinterpret_cast<float4*>(&h.p2.Vs[jw][4 + 4 * qw]) = make_float4(ua[0], ua[1], ua[2], ua[3]);
-                *reinterpret_cast<float4*>(&h.p2.Vs[jw][4 + 4 * (7 - qw)]) = make_float4(ub[0], ub[1], ub[2], ub[3]);
-                if (qw == 0) {
-                    *reinterpret_cast<float4*>(&h.p2.Vs[jw][0]) = *reinterpret_cast<const float4*>(&h.Z[buf][jw][0]);
-                } else if (qw == 1) {
-                    *reinterpret_cast<float4*>(&h.p2.Vs[jw][36]) = make_float4(h.Z[buf][jw][36], 0.0f, 0.0f, 0.0f);
-                }
-            }
-            __syncthreads();
-            SK_PHASE(PH_X1);
-            if (ch + 1 < nchunks) hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), shift);
-            // squared whitened distances, scores, chunk maxima and weights (Eq. (12) with
-            // candidate i left out)
-            if (ntrip <= 8) h5_scores<32>(h, n0, nyq, n, c0, ib);
-            else h5_scores<16>(h, n0, nyq, n, c0, ib);
-            __syncthreads();
-            SK_PHASE(PH_X2);
-            // weighted sums of [x' | u | 1] (online, rescaled by the new maxima)
-            if (ac_act) {
-                const float4 s4 = *reinterpret_cast<const float4*>(&h.p2.scl[4 * ib4]);
+            __syncthreads();  // staged chunk and the previous chunk's weights visible
+            if (ch > 0 && ac_act) {  // weighted sums of [x' | u | 1] of chunk ch-1 (online)
+                const int pb = buf ^ 1, pn = min(kCh, M - c0 + kCh);
+                const float4 s4 = *reinterpret_cast<const float4*>(&h.p2.scl[pb][4 * ib4]);
                 const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) acc[a][q] *= sv[a];
-                for (int j = jg; j < n; j += G) {
-                    const float4 w4 = *reinterpret_cast<const float4*>(&h.p2.Wt[j][4 * ib4]);
-                    const float4 v4 = *reinterpret_cast<const float4*>(&h.p2.Vs[j][4 * kb]);
+                for (int j = jg; j < pn; j += G) {
+                    const float4 w4 = *reinterpret_cast<const float4*>(&h.p2.Wt[pb][j][4 * ib4]);
+                    const float4 v4 = *reinterpret_cast<const float4*>(&h.p2.Vs[pb][j][4 * kb]);
                     const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
                     const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
@@ -1675,6 +1661,28 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
                         for (int q = 0; q < 4; ++q) acc[a][q] = __fmaf_rn(wv[a], vv[q], acc[a][q]);
                 }
             }
+            if (ch == nchunks) break;
+            {   // warp w: coordinate groups (w & 3, 7 - (w & 3)) of candidates 32 (w >> 2) + lane
+                const int qw = wid & 3, jw = lane + 32 * (wid >> 2);
+                float ua[4], ub[4];
+                whiten_quads(h, buf, ny, jw, qw, ua, ub);
+                float* vrow = &h.p2.Vs[buf][jw][0];
+                *reinterpret_cast<float4*>(vrow + 4 + 4 * qw) = make_float4(ua[0], ua[1], ua[2], ua[3]);
+                *reinterpret_cast<float4*>(vrow + 4 + 4 * (7 - qw)) = make_float4(ub[0], ub[1], ub[2], ub[3]);
+                if (qw == 0) {
+                    *reinterpret_cast<float4*>(vrow) = *reinterpret_cast<const float4*>(&h.Z[buf][jw][0]);
+                } else if (qw == 1) {
+                    *reinterpret_cast<float4*>(vrow + 36) = make_float4(h.Z[buf][jw][36], 0.0f, 0.0f, 0.0f);
+                }
+            }
+            __syncthreads();
+            SK_PHASE(PH_X1);
+            if (ch + 1 < nchunks) hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), shift);
+            // squared whitened distances, scores, chunk maxima and weights (Eq. (12) with
+            // candidate i left out)
+            if (ntrip <= 8) h5_scores<32>(h, buf, n0, nyq, n, c0, ib);
+            else h5_scores<16>(h, buf, n0, nyq, n, c0, ib);
+            SK_PHASE(PH_X2);
         }
         __syncthreads();  // Vs / Wt no longer needed: their storage takes the partial sums
         if (ac_act) {
@@ -1686,6 +1694,7 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
         __syncthreads();
         for (int idx = tid; idx < n0 * 37; idx += kThreads) {
             const int i = idx / 37, k = idx - (idx / 37) * 37;
+            if (k >= 4 + ny && k < 36) continue;  // (columns past the context: not computed)
             float a = h.p2.accP[0][i][k];
             for (int g = 1; g < G; ++g) a += h.p2.accP[g][i][k];
             h.accI[i][k] = a;

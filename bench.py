@@ -55,8 +55,9 @@ def parse():
     ap.add_argument("--profile", default="efficient")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=list(WORKLOADS) + ["serve"], default="batch",
-                    help="batch (the benchmark), a smaller case for profiling, or the serving stream")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["serve", "sweep"], default="batch",
+                    help="batch (the benchmark), a smaller case for profiling, the serving stream, "
+                         "or the profile / T_nu sweep")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="serving stream length (20000 = the full 600 frames/s stream of ~33 s)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the occupancy-maximal grid")
@@ -172,7 +173,8 @@ def oracle_params_like(p):
                          ring_step=int(p.ring_step), ridge_rel=float(p.ridge_rel),
                          beta_kmin=int(p.beta_kmin), beta_kmax=int(p.beta_kmax),
                          beta_tie_rel=float(p.beta_tie_rel),
-                         concealed_is_support=int(p.concealed_is_support))
+                         concealed_is_support=int(p.concealed_is_support),
+                         quantize_inloop=1 if (p.flags & 4) else 0)
 
 
 def cpu_baseline(frames, masks, p_gpu, budget_s: float = 25.0):
@@ -239,6 +241,51 @@ def run_reference(args):
                              "sample": "one 352x288 + one 1280x720 frame of the batch per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def measured_peaks_file():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured (MEASURED_PEAKS.json)"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def unit_rooflines(skmmse, st, n_lost, frames, mean_ms, precision, stream):
+    """Fractions of the other units for one step, from the kernel's own counts.
+    - alu: the algorithmic FP32 operations against the FMA rate measured by the library's
+      probe (skmmse_probe_peaks) on this GPU;
+    - exp: exponentials of the method (one per IDL candidate evaluation, |G| per HQL
+      candidate for the beta grid, |I0| per HQL candidate for the leave-one-out pass)
+      against the probed exp2 rate;
+    - tensor: MMA operations issued by the HQL contractions (per 64-candidate chunk:
+      covariance 24 MMAs of 128x48x16, distances 6 of 128x32x16, beta sums 12 of
+      128x48x16) against the measured dense BF16 rate (FP16 runs at the same rate);
+    - hbm: frame bytes read and written per step against the measured copy bandwidth."""
+    pk = skmmse.probe_peaks(stream)
+    peaks, src = measured_peaks_file()
+    sec = mean_ms * 1e-3
+    exps = st["idl_cand_evals"] + st["n_beta"] * st["hql_cands"] + st["hql_i0_cands"]
+    chunks = st["hql_cands"] / 64.0 + 0.5 * st["n_hql"]
+    mma = chunks * (24 * 2 * 128 * 48 * 16 + 6 * 2 * 128 * 32 * 16 + 12 * 2 * 128 * 48 * 16)
+    if precision == "fp32":
+        mma = 0.0
+    hbm_bytes = 2 * sum(f.size for f in frames) + n_lost * (256 * 4 * 2)
+    out = {
+        "alu_probe": {"achieved": st["alg_flops"] / sec / 1e12, "peak": pk["fma_tflops"], "unit": "TFLOP/s",
+                      "frac": st["alg_flops"] / sec / 1e12 / pk["fma_tflops"],
+                      "peak_source": "skmmse_probe_peaks FP32 FMA (measured on this GPU)"},
+        "exp": {"achieved": exps / sec / 1e9, "peak": pk["ex2_per_s"] / 1e9, "unit": "Gexp/s",
+                "frac": exps / sec / pk["ex2_per_s"], "exps_per_step": int(exps),
+                "peak_source": "skmmse_probe_peaks ex2.approx (measured on this GPU)"},
+        "tensor": {"achieved": mma / sec / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                   "frac": mma / sec / 1e12 / peaks["bf16_tflops"], "issued_flops_per_step": mma,
+                   "peak_source": f"dense BF16 burst, {src}; FP16 has the same rate"},
+        "hbm": {"achieved": hbm_bytes / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": hbm_bytes / sec / 1e9 / peaks["hbm_gbs"], "bytes_per_step": int(hbm_bytes),
+                "peak_source": f"copy bandwidth, {src}"},
+    }
+    return out
 
 
 def _time_calls(fn, reps: int, flush, stream) -> float:
@@ -407,6 +454,7 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived)",
                 "alg_flops_per_step": flops}
+    other_rooflines = unit_rooflines(skmmse, st, n_lost, frames, mean_ms, args.precision, stream)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -426,6 +474,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": 4 * args.steps,
             "roofline": roofline,
+            "rooflines_other": other_rooflines,
             "layers": {k: st[k] for k in ("n_patches", "n_brl", "n_idl", "n_hql", "n_brl_nocand")},
             "wall_s_timed": t_wall,
             "clocks": clocks}
@@ -605,10 +654,73 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def ssim(a, b, data_range=255.0):
+    """Mean structural similarity (Gaussian window sigma 1.5, K1 0.01, K2 0.03) of two
+    8-bit images."""
+    from scipy.ndimage import gaussian_filter
+    a = a.astype(np.float64)
+    b = b.astype(np.float64)
+    c1, c2 = (0.01 * data_range) ** 2, (0.03 * data_range) ** 2
+    mu_a, mu_b = gaussian_filter(a, 1.5), gaussian_filter(b, 1.5)
+    saa = gaussian_filter(a * a, 1.5) - mu_a ** 2
+    sbb = gaussian_filter(b * b, 1.5) - mu_b ** 2
+    sab = gaussian_filter(a * b, 1.5) - mu_a * mu_b
+    m = ((2 * mu_a * mu_b + c1) * (2 * sab + c2)) / ((mu_a ** 2 + mu_b ** 2 + c1) * (saa + sbb + c2))
+    return float(m.mean())
+
+
+def run_sweep(args):
+    """Quality against time over the profiles of Table I and a continuous T_nu sweep on the
+    64-frame batch: batch time, PSNR over the lost pixels, SSIM of the whole frame, and the
+    share of patches per layer (the analogue of the paper's profile experiments)."""
+    import torch
+    from paper_2205_11226_gb300 import build as skbuild
+    skbuild.build()
+    from paper_2205_11226_gb300 import skmmse, synth
+    torch.cuda.set_device(0)
+    frames, masks = build_workload(args.seed, "batch")
+    ctx = skmmse.Context()
+    stream = torch.cuda.current_stream()
+    fd = [torch.from_numpy(f).cuda() for f in frames]
+    md = [torch.from_numpy(m).cuda() for m in masks]
+    od = [torch.empty_like(f) for f in fd]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    n_lost = sum(int(m.sum()) for m in masks)
+    settings = [("express", {}), ("efficient", {}), ("excellent", {})]
+    settings += [("efficient", {"t_nu": t}) for t in (0.003, 0.03, 0.3, 1.0, 3.0, 10.0)]
+    rows = []
+    for prof, kw in settings:
+        p = skmmse.params(prof, precision=PRECISIONS[args.precision], **kw)
+        ms_ = _time_calls(lambda: ctx.conceal_batch(fd, md, p, outs=od, stream=stream), 3, flush, stream)
+        _, st = ctx.conceal_batch(fd, md, p, outs=od, stats=True, stream=stream)
+        torch.cuda.synchronize()
+        outs = [o.cpu().numpy() for o in od]
+        lost_err = np.concatenate([(o.astype(np.float64) - f)[synth.lost_pixel_mask(m, f.shape[1], f.shape[0])]
+                                   for o, f, m in zip(outs, frames, masks)])
+        mse = float(np.mean(lost_err ** 2))
+        npatch = max(1, st["n_patches"])
+        rows.append({"profile": prof, "t_phi": float(p.t_phi), "t_nu": float(p.t_nu), "ms": ms_,
+                     "mbs_per_s": n_lost / (ms_ * 1e-3),
+                     "psnr_lost_db": 10.0 * np.log10(255.0 ** 2 / mse) if mse > 0 else float("inf"),
+                     "ssim_frame_mean": float(np.mean([ssim(o, f) for o, f in zip(outs, frames)])),
+                     "share_brl": (st["n_brl"] + st["n_empty"] + st["n_brl_nocand"]) / npatch,
+                     "share_idl": st["n_idl"] / npatch, "share_hql": st["n_hql"] / npatch})
+    line = {"metric": "profile sweep: concealment time and quality", "unit": "ms", "n_gpus": 1,
+            "dtype": DTYPES[args.precision], "data": "synthetic (seeded generator; no dataset)",
+            "config": {"workload": WORKLOADS["batch"], "precision": args.precision,
+                       "l2": "flushed between timed calls (256 MiB write)"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.workload == "serve":
         run_serve(args)
+        return
+    if args.workload == "sweep":
+        run_sweep(args)
         return
     if args.impl == "reference":
         run_reference(args)

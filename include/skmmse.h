@@ -82,6 +82,11 @@ typedef enum { SKMMSE_EXPRESS = 0, SKMMSE_EFFICIENT = 1, SKMMSE_EXCELLENT = 2 } 
    carry the kernel's own estimates, so each step can be compared with a reference on
    identical inputs.  Outputs then hold the reference values.  Not for production use. */
 #define SKMMSE_FLAG_FORCE 2u
+/* In-loop 8-bit quantisation: every estimate is written back into the support rounded to
+   the nearest integer (ties to even), as a decoder that keeps 8-bit frames does; the
+   reading of the end of Sec. III that keeps unrounded values is the default.  Later
+   templates then hold integers only.  Trace records keep the unrounded estimate. */
+#define SKMMSE_FLAG_QUANTIZE 4u
 
 typedef struct {
     float t_phi;        /* flatness threshold T_phi, Eq. (17) / Table I; BRL iff phi <= T_phi */
@@ -251,6 +256,14 @@ skmmse_status skmmse_conceal_noalloc(const uint8_t* d_frame, int width, int heig
    8 beta grid, 9 I0, 10 leave-one-out pass, 11 HQL estimate, 12 write-back, 13 publish.
    All zero unless the library was built with -DSKMMSE_PHASE_CLOCKS.  Synchronises. */
 skmmse_status skmmse_read_phase_clocks(skmmse_context* ctx, long long* h_clocks16, void* stream);
+
+/* Diagnostic (the paper has no counterpart): measured throughput of the current device's
+   FP32 FMA pipe (*h_fma_tflops, TFLOP/s, 2 FLOP per FMA) and of its exp2 unit
+   (*h_ex2_per_s, ex2.approx per second), from two short saturating kernels (8 CTAs of 256
+   threads per SM, 8 independent chains per thread) timed with CUDA events on `stream`.
+   The benchmark divides by them for its ALU and exp roofline fractions.  Allocates and
+   frees a small device buffer; synchronises. */
+skmmse_status skmmse_probe_peaks(double* h_fma_tflops, double* h_ex2_per_s, void* stream);
 
 #ifdef __cplusplus
 }

@@ -40,6 +40,7 @@ class Params(ctypes.Structure):
         ("beta_tie_rel", ctypes.c_double),
         ("concealed_is_support", ctypes.c_int),
         ("store_f32", ctypes.c_int),
+        ("quantize_inloop", ctypes.c_int),
     ]
 
 
@@ -76,7 +77,7 @@ def params(profile: str = "efficient", **kw) -> Params:
     t_phi, t_nu = PROFILES[profile]
     p = Params(t_phi=t_phi, t_nu=t_nu, sigma2=10.0, ring_step=4, ridge_rel=1e-3,
                beta_kmin=-8, beta_kmax=16, beta_tie_rel=1e-3, concealed_is_support=1,
-               store_f32=0)
+               store_f32=0, quantize_inloop=0)
     for k, v in kw.items():
         setattr(p, k, v)
     return p

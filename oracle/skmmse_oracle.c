@@ -44,7 +44,8 @@
  *       (ties to the lower index); leave-one-out predictions for i in I0; the alpha that
  *       minimises Eq. (11) in closed form, clamped to [0, 1] (0 if undefined).
  *   R8  every estimate is clipped to [0, 255] and written back unrounded (store_f32:
- *       rounded to binary32, to give a binary32 path under test identical inputs).
+ *       rounded to binary32, to give a binary32 path under test identical inputs;
+ *       quantize_inloop: rounded to the nearest integer, ties to even).
  */
 #include <math.h>
 #include <pthread.h>
@@ -71,6 +72,9 @@ typedef struct {
     int concealed_is_support; /* R1 */
     int store_f32;       /* R8 variant: reconstructions are stored rounded to binary32 (the
                             storage precision of a path under test); arithmetic stays FP64 */
+    int quantize_inloop; /* R8 variant: every estimate is written back into the support
+                            rounded to an 8-bit integer (round half to even), as a decoder
+                            that keeps 8-bit frames does; the trace keeps the estimate */
 } oracle_params;
 
 typedef struct {
@@ -551,7 +555,7 @@ static void conceal_block(oracle_job* job, oracle_scratch* s, int by, int bx) {
         for (int a = 0; a < 4; a++) {
             xhat[a] = clip255(xhat[a]);
             if (p->store_f32) xhat[a] = (double)(float)xhat[a];
-            s->R[fr[a]][fc[a]] = xhat[a];
+            s->R[fr[a]][fc[a]] = p->quantize_inloop ? nearbyint(xhat[a]) : xhat[a];
             s->A[fr[a]][fc[a]] = 1;
         }
         filled[pa][pb] = 1;

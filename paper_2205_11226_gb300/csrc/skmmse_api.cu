@@ -14,6 +14,7 @@
 
 #include "skmmse.h"
 #include "skmmse_kernel.cuh"
+#include "probe.cuh"
 
 using sk::FrameDev;
 using sk::KParams;
@@ -68,7 +69,7 @@ skmmse_status validate_params(const skmmse_params* p) {
     if (p->precision != SKMMSE_FP32 && p->precision != SKMMSE_MIXED_BF16 &&
         p->precision != SKMMSE_MIXED_FP16)
         return SKMMSE_ERR_ARG;
-    if (p->flags & ~(SKMMSE_FLAG_TRACE | SKMMSE_FLAG_FORCE)) return SKMMSE_ERR_ARG;
+    if (p->flags & ~(SKMMSE_FLAG_TRACE | SKMMSE_FLAG_FORCE | SKMMSE_FLAG_QUANTIZE)) return SKMMSE_ERR_ARG;
     if ((p->flags & SKMMSE_FLAG_FORCE) && !(p->flags & SKMMSE_FLAG_TRACE)) return SKMMSE_ERR_ARG;
     return SKMMSE_OK;
 }
@@ -646,7 +647,7 @@ skmmse_status skmmse_conceal_noalloc(const uint8_t* d_frame, int width, int heig
     f.out_f32_pitch = width;
     skmmse_status s = validate_params(p);
     if (s != SKMMSE_OK) return s;
-    if (p->flags != 0) return SKMMSE_ERR_ARG;  // no trace buffer on this entry point
+    if (p->flags & ~SKMMSE_FLAG_QUANTIZE) return SKMMSE_ERR_ARG;  // no trace buffer here
     s = validate_frame(f);
     if (s != SKMMSE_OK) return s;
     const long long mbw = (width + 15) / 16, mbh = (height + 15) / 16;
@@ -743,6 +744,43 @@ skmmse_status skmmse_read_phase_clocks(skmmse_context* c, long long* h_clocks16,
                              static_cast<cudaStream_t>(stream_v)));
     SK_CHECK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream_v)));
     for (int i = 0; i < sk::kNPhase; ++i) h_clocks16[i] = (long long)raw[i];
+    return SKMMSE_OK;
+}
+
+
+skmmse_status skmmse_probe_peaks(double* h_fma_tflops, double* h_ex2_per_s, void* stream_v) {
+    if (!h_fma_tflops || !h_ex2_per_s) return SKMMSE_ERR_ARG;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    int dev = 0, sms = 0;
+    SK_CHECK(cudaGetDevice(&dev));
+    SK_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8, threads = 256;  // 8 CTAs of 256 threads per SM: full occupancy
+    float* d_out = nullptr;
+    SK_CHECK(cudaMalloc(&d_out, sizeof(float) * blocks * threads));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float ms_fma = 0.0f, ms_ex2 = 0.0f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first round warms up
+        cudaEventRecord(e0, stream);
+        sk::probe_fma_kernel<<<blocks, threads, 0, stream>>>(d_out, 0.999f, 1e-3f);
+        cudaEventRecord(e1, stream);
+        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_fma, e0, e1);
+        if (e != cudaSuccess) break;
+        cudaEventRecord(e0, stream);
+        sk::probe_ex2_kernel<<<blocks, threads, 0, stream>>>(d_out, 0.5f);
+        cudaEventRecord(e1, stream);
+        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_ex2, e0, e1);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d_out);
+    if (e != cudaSuccess || ms_fma <= 0.0f || ms_ex2 <= 0.0f) return cuda_fail(e);
+    const double thr = (double)blocks * threads * sk::kProbeIters * sk::kProbeChains;
+    *h_fma_tflops = thr * 2.0 / (ms_fma * 1e-3) / 1e12;
+    *h_ex2_per_s = thr / (ms_ex2 * 1e-3);
     return SKMMSE_OK;
 }
 

@@ -1883,6 +1883,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const bool trace_on = (P.flags & 1u) != 0u;
     const bool force_on = (P.flags & 2u) != 0u;
+    const bool quant_on = (P.flags & 4u) != 0u;  // in-loop 8-bit quantisation
 
     if (tid == 0) {
         mbar_init(&sm.mbar, 1);
@@ -2025,6 +2026,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                     if (lane < 4) {
                         float xw = fminf(fmaxf(xv, 0.0f), 255.0f);
                         if (force_on && trace_base) xw = trace_base[step].x[lane];  // verification hook
+                        if (quant_on) xw = rintf(xw);
                         sm.S[(pr + (lane >> 1)) * kReg + pc + (lane & 1)] = xw;
                     }
                     if (lane == 0) {
@@ -2136,6 +2138,10 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                 if (force_on && trace_base) {  // verification hook: reference write-back
 #pragma unroll
                     for (int a = 0; a < 4; ++a) xw[a] = trace_base[step].x[a];
+                }
+                if (quant_on) {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) xw[a] = rintf(xw[a]);
                 }
                 sm.S[pr * kReg + pc] = xw[0];
                 sm.S[pr * kReg + pc + 1] = xw[1];

@@ -21,6 +21,7 @@ PROFILES = {"express": EXPRESS, "efficient": EFFICIENT, "excellent": EXCELLENT}
 FP32, MIXED_BF16, MIXED_FP16 = 0, 1, 2
 FLAG_TRACE = 1
 FLAG_FORCE = 2
+FLAG_QUANTIZE = 4
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported frame shape", 3: "unsupported alignment",
           4: "device memory allocation failed", 5: "CUDA runtime error",
@@ -73,6 +74,7 @@ TRACE_DTYPE = np.dtype([
 EXPORTS = ["skmmse_abi_version", "skmmse_struct_size", "skmmse_status_str", "skmmse_params_preset",
            "skmmse_create", "skmmse_destroy", "skmmse_conceal", "skmmse_conceal_batch",
            "skmmse_read_stats", "skmmse_read_phase_clocks", "skmmse_conceal_noalloc",
+           "skmmse_probe_peaks",
            "skmmse_graph_create", "skmmse_graph_launch", "skmmse_graph_read_stats",
            "skmmse_graph_destroy", "skmmse_autotune", "skmmse_set_ctas_per_sm"]
 
@@ -130,6 +132,8 @@ def load(path: str = LIB_PATH):
                                     ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ci)]
     lib.skmmse_set_ctas_per_sm.restype = ci
     lib.skmmse_set_ctas_per_sm.argtypes = [vp, ci]
+    lib.skmmse_probe_peaks.restype = ci
+    lib.skmmse_probe_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     lib.skmmse_read_phase_clocks.restype = ci
     lib.skmmse_read_phase_clocks.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), vp]
     assert lib.skmmse_struct_size(0) == TRACE_DTYPE.itemsize, "trace record layout"
@@ -147,6 +151,15 @@ def params(profile: str | int = "efficient", **kw) -> Params:
     for k, v in kw.items():
         setattr(p, k, v)
     return p
+
+
+def probe_peaks(stream=None) -> dict:
+    """Measured FP32 FMA (TFLOP/s) and exp2 (per second) throughput of the current device."""
+    lib = load()
+    fma, ex2 = ctypes.c_double(), ctypes.c_double()
+    _check(lib.skmmse_probe_peaks(ctypes.byref(fma), ctypes.byref(ex2), _stream_handle(stream)),
+           "skmmse_probe_peaks")
+    return {"fma_tflops": fma.value, "ex2_per_s": ex2.value}
 
 
 def _check(status: int, where: str):

@@ -34,7 +34,8 @@ def matching_oracle_params(p: skmmse.Params, store_f32: int = 0) -> oracle.Param
                          ring_step=int(p.ring_step), ridge_rel=float(p.ridge_rel),
                          beta_kmin=int(p.beta_kmin), beta_kmax=int(p.beta_kmax),
                          beta_tie_rel=float(p.beta_tie_rel),
-                         concealed_is_support=int(p.concealed_is_support))
+                         concealed_is_support=int(p.concealed_is_support),
+                         quantize_inloop=1 if (p.flags & skmmse.FLAG_QUANTIZE) else 0)
 
 
 def in_frame_patches(by, bx, W, H):

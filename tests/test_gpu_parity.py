@@ -168,3 +168,21 @@ def test_mixed_checkerboard_and_chains(gpu_ctx, precision):
     f = synth.make_frame(256, 160, 8, fine_texture=True)
     m = synth.loss_runs(256, 160, 3, 0.25)
     check(f, m, skmmse.params("efficient", precision=precision), gpu_ctx, tol=TOL_MIXED)
+
+
+# ---------------------------------------------------------------------------------------
+# in-loop 8-bit quantisation (SKMMSE_FLAG_QUANTIZE): estimates written back rounded.
+# Teacher-forced only: free-running, an estimate within 1e-4 of a half-integer may round
+# the other way and the 1-gray difference travels down the chain.
+
+@pytest.mark.parametrize("precision,tol", [(skmmse.FP32, None), (skmmse.MIXED_FP16, TOL_MIXED)])
+def test_quantize_inloop(gpu_ctx, precision, tol):
+    f = synth.make_frame(256, 160, 8, fine_texture=True)
+    m = synth.loss_runs(256, 160, 3, 0.25)
+    p = skmmse.params("efficient", precision=precision, flags=skmmse.FLAG_QUANTIZE)
+    rep, gpu, orc = check(f, m, p, gpu_ctx, free=False, tol=tol)
+    assert np.array_equal(gpu["out_f32"], np.rint(gpu["out_f32"]))
+    g = skmmse.conceal_numpy(f, m, p, ctx=gpu_ctx)
+    assert np.array_equal(g["out_f32"], np.rint(g["out_f32"]))
+    lost = synth.lost_pixel_mask(m, f.shape[1], f.shape[0])  # out_f32: concealed pixels only
+    assert np.array_equal(g["out"][lost].astype(np.float32), g["out_f32"][lost])

@@ -316,3 +316,40 @@ def test_hql_first_patch_matches_numpy_brute_force(seed):
     assert abs(a_cf - t0["alpha"]) < 1e-9
     assert abs(a_scan - a_cf) <= 1e-4  # the closed form is the minimiser of Eq. (11)
     assert np.max(np.abs(np.clip(xhat, 0, 255) - t0["x"])) < 1e-8
+
+
+# ---------------------------------------------------------------------------------------
+# In-loop 8-bit quantisation (variant of R8): estimates are written back rounded
+
+def test_quantize_inloop_writes_back_rounded_estimates():
+    # every output value is the round-half-even of the estimate the trace records for
+    # that pixel, and later steps read those integers back
+    f = synth.make_frame(96, 96, 31, fine_texture=True)
+    m = np.zeros((6, 6), np.uint8)
+    m[2, 2] = m[2, 3] = m[3, 2] = 1  # a small chain: later blocks read rounded values
+    p = oracle.params("excellent", quantize_inloop=1)
+    r = oracle.conceal(f, m, p, trace=True)
+    out, tr = r["out"], r["trace"]
+    assert np.array_equal(out, np.rint(out))
+    lost = [(y, x) for y in range(6) for x in range(6) if m[y, x]]
+    for rank, (by, bx) in enumerate(lost):
+        for rec in tr[rank]:
+            a, b = int(rec["patch"]) >> 3, int(rec["patch"]) & 7
+            y, x = by * 16 + 2 * a, bx * 16 + 2 * b
+            est = np.asarray(rec["x"], np.float64).reshape(2, 2)
+            assert np.array_equal(out[y:y + 2, x:x + 2], np.rint(est))
+    # the unrounded variant differs (the estimates are not all integers here)
+    r0 = oracle.conceal(f, m, oracle.params("excellent"), trace=True)
+    assert not np.array_equal(r0["out"], out)
+
+
+def test_quantize_inloop_is_a_no_op_when_estimates_are_integers():
+    # sigma^2 -> 0 on a periodic texture copies exact integer matches: rounding changes
+    # nothing, so both variants give the same frame and the same decisions
+    f = periodic_frame()
+    m = isolated(f, 3, 3)
+    kw = dict(t_phi=-1.0, t_nu=0.5, sigma2=1e-9)
+    a = oracle.conceal(f, m, oracle.params("efficient", **kw), trace=True)
+    b = oracle.conceal(f, m, oracle.params("efficient", quantize_inloop=1, **kw), trace=True)
+    assert np.array_equal(a["out"], b["out"])
+    assert np.array_equal(a["trace"]["layer"], b["trace"]["layer"])

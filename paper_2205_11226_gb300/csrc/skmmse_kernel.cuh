@@ -410,12 +410,12 @@ __device__ __forceinline__ void annulus_pos(int i, int rin, int rout, int* dy, i
 __device__ __forceinline__ void online_add(float s, float x0, float x1, float x2, float x3,
                                            float& m, float& s0, float sx[4]) {
     if (s > m) {
-        const float sc = expf(m - s);
+        const float sc = __expf(m - s);
         s0 *= sc;
         sx[0] *= sc; sx[1] *= sc; sx[2] *= sc; sx[3] *= sc;
         m = s;
     }
-    const float w = expf(s - m);
+    const float w = __expf(s - m);
     s0 += w;
     sx[0] = __fmaf_rn(w, x0, sx[0]);
     sx[1] = __fmaf_rn(w, x1, sx[1]);
@@ -550,7 +550,7 @@ __device__ __forceinline__ IdlOut idl_step(const KParams& P, int wr, int wc,
         float wm = m;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
-        const float lsc = expf(m - wm);
+        const float lsc = __expf(m - wm);
         float ws = s0 * lsc, wx[4] = {sx[0] * lsc, sx[1] * lsc, sx[2] * lsc, sx[3] * lsc};
         int wc = cnt;
 #pragma unroll
@@ -577,7 +577,7 @@ __device__ __forceinline__ IdlOut idl_step(const KParams& P, int wr, int wc,
         int bc = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) {
-            const float e = expf(slot[w].m - bm);
+            const float e = __expf(slot[w].m - bm);
             bs = __fmaf_rn(slot[w].s0, e, bs);
 #pragma unroll
             for (int q = 0; q < 4; ++q) bx[q] = __fmaf_rn(slot[w].sx[q], e, bx[q]);
@@ -1018,7 +1018,7 @@ __device__ __noinline__ void h3_mixed(const KParams& P, int M, int nz, float shi
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                     const int j = 8 * g8 + t;
-                    v[t] = j < n ? expf(-(h.d[c0 + j] - dmin) * ib) : 0.0f;
+                    v[t] = j < n ? __expf(-(h.d[c0 + j] - dmin) * ib) : 0.0f;
                 }
                 store8_split<BF16>(h.mx.t2, h.mx.t3, b, 8 * g8, 64, v);
             }
@@ -1101,9 +1101,9 @@ __device__ __forceinline__ void h5_scores(Hql& h, int vb_, int n0, int nyq, int 
         const float mnew = fmaxf(mold[a], mx[a]);
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            h.p2.Wt[vb_][jq + L * r][i] = sc[a][r] == -INFINITY ? 0.0f : expf(sc[a][r] - mnew);
+            h.p2.Wt[vb_][jq + L * r][i] = sc[a][r] == -INFINITY ? 0.0f : __expf(sc[a][r] - mnew);
         if (jq == 0) {
-            h.p2.scl[vb_][i] = mold[a] == -INFINITY ? 0.0f : expf(mold[a] - mnew);
+            h.p2.scl[vb_][i] = mold[a] == -INFINITY ? 0.0f : __expf(mold[a] - mnew);
             h.p2.mrow[i] = mnew;
         }
     }
@@ -1440,7 +1440,7 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
             __syncthreads();
             if (act) {
                 for (int j = g; j < n; j += G3) {
-                    const float w = expf(-(h.d[c0 + j] - dmin) * ib);
+                    const float w = __expf(-(h.d[c0 + j] - dmin) * ib);
 #pragma unroll
                     for (int k4 = 0; k4 < kZs / 4; ++k4) {
                         if (k4 >= kql3 && k4 != 9) continue;  // columns past the context are zero

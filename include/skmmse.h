@@ -87,6 +87,12 @@ typedef enum { SKMMSE_EXPRESS = 0, SKMMSE_EFFICIENT = 1, SKMMSE_EXCELLENT = 2 } 
    reading of the end of Sec. III that keeps unrounded values is the default.  Later
    templates then hold integers only.  Trace records keep the unrounded estimate. */
 #define SKMMSE_FLAG_QUANTIZE 4u
+/* Test hook for failure detection: a CTA that finds no ready block gives up after 64
+   polls without progress instead of ~2^25 (about 9 s).  On a workload with dependency
+   chains idle CTAs then give up while others still work: the call still conceals every
+   block (the working CTAs take the rest), sets the device error word and returns
+   SKMMSE_ERR_TIMEOUT, and the context stays usable.  Not for production use. */
+#define SKMMSE_FLAG_SHORT_WAITS 8u
 
 typedef struct {
     float t_phi;        /* flatness threshold T_phi, Eq. (17) / Table I; BRL iff phi <= T_phi */

@@ -69,7 +69,8 @@ skmmse_status validate_params(const skmmse_params* p) {
     if (p->precision != SKMMSE_FP32 && p->precision != SKMMSE_MIXED_BF16 &&
         p->precision != SKMMSE_MIXED_FP16)
         return SKMMSE_ERR_ARG;
-    if (p->flags & ~(SKMMSE_FLAG_TRACE | SKMMSE_FLAG_FORCE | SKMMSE_FLAG_QUANTIZE)) return SKMMSE_ERR_ARG;
+    if (p->flags & ~(SKMMSE_FLAG_TRACE | SKMMSE_FLAG_FORCE | SKMMSE_FLAG_QUANTIZE | SKMMSE_FLAG_SHORT_WAITS))
+        return SKMMSE_ERR_ARG;
     if ((p->flags & SKMMSE_FLAG_FORCE) && !(p->flags & SKMMSE_FLAG_TRACE)) return SKMMSE_ERR_ARG;
     return SKMMSE_OK;
 }
@@ -105,6 +106,7 @@ KParams make_kparams(const skmmse_params* p) {
     k.concealed_is_support = p->concealed_is_support ? 1 : 0;
     k.flags = p->flags;
     k.mixed = p->precision;
+    k.claim_idle_limit = (p->flags & SKMMSE_FLAG_SHORT_WAITS) ? 64u : (1u << 25);
     return k;
 }
 

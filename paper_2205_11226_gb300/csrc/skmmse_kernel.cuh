@@ -94,6 +94,7 @@ struct KParams {
     int concealed_is_support;
     unsigned flags;
     int mixed;            // 0: FP32 on the CUDA cores; 1: BF16, 2: FP16 tensor-core contractions
+    unsigned claim_idle_limit;  // polls without progress before a CTA gives up claiming
 };
 
 struct FrameDev {
@@ -1790,7 +1791,7 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
 // Ready queue (see the work-queue notes below the kernel).  Called by warp 0 of a CTA;
 // returns the claimed entry, -1 when every entry is claimed, -2 on a timeout (error word
 // set).  The bound counts idle rounds without progress of the whole call.
-__device__ __noinline__ int claim_ready(const WorkDev& W, int n_entries) {
+__device__ __noinline__ int claim_ready(const WorkDev& W, int n_entries, unsigned idle_limit) {
     const int lane = threadIdx.x & 31;
     unsigned idle = 0;
     int seen = -1;
@@ -1845,7 +1846,7 @@ __device__ __noinline__ int claim_ready(const WorkDev& W, int n_entries) {
         }
         if (lost_race) continue;
         __nanosleep(256);
-        if (++idle > (1u << 25)) {
+        if (++idle > idle_limit) {
             if (lane == 0) atomicExch(&W.counters[2], 6);
             return -2;
         }
@@ -1903,7 +1904,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
 
     for (;;) {
         if (wid == 0) {
-            const int got = claim_ready(W, n_entries);
+            const int got = claim_ready(W, n_entries, P.claim_idle_limit);
             if (lane == 0) sm.entry = got;
         }
         __syncthreads();

@@ -22,6 +22,7 @@ FP32, MIXED_BF16, MIXED_FP16 = 0, 1, 2
 FLAG_TRACE = 1
 FLAG_FORCE = 2
 FLAG_QUANTIZE = 4
+FLAG_SHORT_WAITS = 8
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported frame shape", 3: "unsupported alignment",
           4: "device memory allocation failed", 5: "CUDA runtime error",

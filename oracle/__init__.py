@@ -108,6 +108,11 @@ def _load():
             ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
             ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_void_p,
             ctypes.POINTER(Stats), ctypes.c_int]
+        lib.oracle_conceal_px.restype = ctypes.c_int
+        lib.oracle_conceal_px.argtypes = [
+            ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+            ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_void_p,
+            ctypes.POINTER(Stats), ctypes.c_int]
         assert lib.oracle_trace_rec_size() == ctypes.sizeof(TraceRec)
         assert lib.oracle_stats_size() == ctypes.sizeof(Stats)
         _lib = lib
@@ -126,19 +131,37 @@ def trace_to_numpy(buf) -> np.ndarray:
     return np.frombuffer(buf, dtype=dt)
 
 
-def conceal(frame: np.ndarray, mb_lost: np.ndarray, p: Params | None = None, *,
-            select: np.ndarray | None = None, trace: bool = False, threads: int = 1):
+def blocks_of(px_lost: np.ndarray) -> np.ndarray:
+    """Block flags of a per-pixel loss mask: a block is worked on iff it holds a lost pixel."""
+    px = np.asarray(px_lost) != 0
+    H, W = px.shape
+    mbh, mbw = (H + 15) // 16, (W + 15) // 16
+    pad = np.zeros((mbh * 16, mbw * 16), dtype=bool)
+    pad[:H, :W] = px
+    return pad.reshape(mbh, 16, mbw, 16).any(axis=(1, 3)).astype(np.uint8)
+
+
+def conceal(frame: np.ndarray, mb_lost: np.ndarray | None, p: Params | None = None, *,
+            px_lost: np.ndarray | None = None, select: np.ndarray | None = None,
+            trace: bool = False, threads: int = 1):
     """Conceal the lost 16x16 blocks of one 8-bit frame.
 
-    frame: uint8 [H, W]; mb_lost: uint8/bool [ceil(H/16), ceil(W/16)], 1 = lost.
+    frame: uint8 [H, W]; mb_lost: uint8/bool [ceil(H/16), ceil(W/16)], 1 = lost; or, for
+    an arbitrarily shaped loss, mb_lost None and px_lost: uint8/bool [H, W], 1 = lost.
     Returns dict(out=float64 [H, W], stats=dict, trace=structured array or None).
-    Trace records are indexed [rank among lost blocks in raster order, step].
+    Trace records are indexed [rank among lost blocks in raster order, step]; with px_lost
+    the lost blocks are those holding a lost pixel.
     """
     lib = _load()
     p = p if p is not None else params()
     frame = np.ascontiguousarray(frame, dtype=np.uint8)
     H, W = frame.shape
     mbh, mbw = (H + 15) // 16, (W + 15) // 16
+    if px_lost is not None:
+        assert mb_lost is None, "give either mb_lost or px_lost"
+        px_lost = np.ascontiguousarray(np.asarray(px_lost) != 0, dtype=np.uint8)
+        assert px_lost.shape == (H, W), (px_lost.shape, (H, W))
+        mb_lost = blocks_of(px_lost)
     mb_lost = np.ascontiguousarray(mb_lost, dtype=np.uint8)
     assert mb_lost.shape == (mbh, mbw), (mb_lost.shape, (mbh, mbw))
     sel = None
@@ -151,10 +174,16 @@ def conceal(frame: np.ndarray, mb_lost: np.ndarray, p: Params | None = None, *,
     if trace:
         tbuf = (TraceRec * max(1, nlost * 64))()
     st = Stats()
-    rc = lib.oracle_conceal(frame.ctypes.data, W, H, W, mb_lost.ctypes.data,
-                            None if sel is None else sel.ctypes.data, ctypes.byref(p),
-                            out.ctypes.data, None if tbuf is None else ctypes.addressof(tbuf),
-                            ctypes.byref(st), int(threads))
+    sel_p = None if sel is None else sel.ctypes.data
+    tb_p = None if tbuf is None else ctypes.addressof(tbuf)
+    if px_lost is None:
+        rc = lib.oracle_conceal(frame.ctypes.data, W, H, W, mb_lost.ctypes.data, sel_p,
+                                ctypes.byref(p), out.ctypes.data, tb_p, ctypes.byref(st),
+                                int(threads))
+    else:
+        rc = lib.oracle_conceal_px(frame.ctypes.data, W, H, W, px_lost.ctypes.data, W, sel_p,
+                                   ctypes.byref(p), out.ctypes.data, tb_p, ctypes.byref(st),
+                                   int(threads))
     if rc != 0:
         raise ValueError(f"oracle_conceal rejected the arguments (rc={rc})")
     stats = {k: (list(getattr(st, k)) if k == "idl_ring_hist" else int(getattr(st, k)))

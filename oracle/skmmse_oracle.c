@@ -46,6 +46,14 @@
  *   R8  every estimate is clipped to [0, 255] and written back unrounded (store_f32:
  *       rounded to binary32, to give a binary32 path under test identical inputs;
  *       quantize_inloop: rounded to the nearest integer, ties to even).
+ *   R9  arbitrarily shaped loss (Sec. II: the method extends to any loss shape), given as
+ *       a per-pixel mask: the unit of work stays the 16x16 block, and a block is worked on
+ *       iff it holds a lost pixel; dependencies and R1 apply to those blocks.  Received
+ *       pixels are available wherever they lie.  The patches to fill are the 2x2 patches
+ *       of the block's grid holding a lost pixel.  x0 keeps the 2x2 shape of Fig. 1(a):
+ *       its received pixels are not context (y0 never includes the patch itself, and the
+ *       R2 count is over the 6x6 window less the patch), and only its lost pixels take
+ *       the estimate.  With every pixel of a lost block lost this is the block method.
  */
 #include <math.h>
 #include <pthread.h>
@@ -112,6 +120,7 @@ typedef struct {
 typedef struct {
     const uint8_t* frame; int W, H, pitch;
     const uint8_t* mb_lost; int mbw, mbh;
+    const uint8_t* px_lost; int px_pitch; /* R9: per-pixel loss, or NULL (whole blocks) */
     const oracle_params* p;
     double* out;               /* W*H values */
     int32_t* lost_index;       /* per block: raster rank among lost blocks, -1 received */
@@ -138,6 +147,15 @@ static int popcount_window(unsigned char A[OR_REG][OR_REG], int r0, int c0) {
 }
 
 static double clip255(double v) { return v < 0.0 ? 0.0 : (v > 255.0 ? 255.0 : v); }
+
+/* is frame pixel (fy, fx) lost: its block's flag, or its own flag under R9 */
+static int pixel_lost(const oracle_job* job, int fy, int fx) {
+    if (job->px_lost) return job->px_lost[(size_t)fy * job->px_pitch + fx] != 0;
+    return job->mb_lost[(fy / OR_MB) * job->mbw + fx / OR_MB] != 0;
+}
+
+/* is window position (r, c) of a 6x6 window one of the patch's own four positions */
+static int in_patch(int r, int c) { return (r == 2 || r == 3) && (c == 2 || c == 3); }
 
 /* Cholesky factorisation of an n x n SPD matrix (row-major, lda = n): A = L L^T. */
 static int cholesky(double* a, int n) {
@@ -389,7 +407,7 @@ static void conceal_block(oracle_job* job, oracle_scratch* s, int by, int bx) {
             if (fy < 0 || fx < 0 || fy >= H || fx >= W) continue;
             int nb = (fy / OR_MB) * job->mbw + fx / OR_MB;
             int rank = job->lost_index[nb];
-            if (rank < 0) {
+            if (rank < 0 || !pixel_lost(job, fy, fx)) { /* received (R9: wherever it lies) */
                 s->R[r][c] = job->frame[(size_t)fy * job->pitch + fx];
                 s->A[r][c] = 1;
             } else if (p->concealed_is_support && rank < my_rank) {
@@ -398,34 +416,41 @@ static void conceal_block(oracle_job* job, oracle_scratch* s, int by, int bx) {
             }
         }
 
-    /* patches of this block that lie in the frame */
+    /* patches of this block to fill: in the frame and holding a lost pixel (R9) */
     unsigned char filled[8][8], inframe[8][8];
     int npatch = 0;
     for (int a = 0; a < 8; a++)
         for (int b = 0; b < 8; b++) {
             filled[a][b] = 0;
-            inframe[a][b] = (by * OR_MB + 2 * a < H) && (bx * OR_MB + 2 * b < W);
+            const int fy = by * OR_MB + 2 * a, fx = bx * OR_MB + 2 * b;
+            inframe[a][b] = fy < H && fx < W &&
+                            (pixel_lost(job, fy, fx) || pixel_lost(job, fy, fx + 1) ||
+                             pixel_lost(job, fy + 1, fx) || pixel_lost(job, fy + 1, fx + 1));
             npatch += inframe[a][b];
         }
 
     for (int step = 0; step < npatch; step++) {
-        /* R2: most available pixels in the 6x6 window, ties to the lowest index */
+        /* R2: most available pixels in the 6x6 window less the patch (R9), ties to the
+           lowest index */
         int pa = -1, pb = -1, best = -1;
         for (int a = 0; a < 8; a++)
             for (int b = 0; b < 8; b++) {
                 if (!inframe[a][b] || filled[a][b]) continue;
-                int n = popcount_window(s->A, OR_MB + 2 * a - 2, OR_MB + 2 * b - 2);
+                const int r0 = OR_MB + 2 * a, c0 = OR_MB + 2 * b;
+                int n = popcount_window(s->A, r0 - 2, c0 - 2) - s->A[r0][c0] - s->A[r0][c0 + 1] -
+                        s->A[r0 + 1][c0] - s->A[r0 + 1][c0 + 1];
                 if (n > best) { best = n; pa = a; pb = b; }
             }
         const int pr = OR_MB + 2 * pa, pc = OR_MB + 2 * pb; /* patch top-left, region coords */
         const int wr = pr - 2, wc = pc - 2;                  /* window top-left */
 
-        /* context y0: available pixels of the 6x6 window in window raster order (Sec. II) */
+        /* context y0: available pixels of the 6x6 window outside the patch, in window
+           raster order (Sec. II, R9) */
         double y0[36];
         int yr[36], yc[36], ny = 0;
         for (int r = 0; r < OR_WIN; r++)
             for (int c = 0; c < OR_WIN; c++)
-                if (s->A[wr + r][wc + c]) {
+                if (!in_patch(r, c) && s->A[wr + r][wc + c]) {
                     y0[ny] = s->R[wr + r][wc + c];
                     yr[ny] = r;
                     yc[ny] = c;
@@ -550,11 +575,13 @@ static void conceal_block(oracle_job* job, oracle_scratch* s, int by, int bx) {
                 }
             }
         }
-        /* R8: clip, write back into the support (end of Sec. III) */
+        /* R8: clip, write back into the support (end of Sec. III); R9: the lost pixels of
+           the patch only (they are the unavailable ones) */
         const int fr[4] = {pr, pr, pr + 1, pr + 1}, fc[4] = {pc, pc + 1, pc, pc + 1};
         for (int a = 0; a < 4; a++) {
             xhat[a] = clip255(xhat[a]);
             if (p->store_f32) xhat[a] = (double)(float)xhat[a];
+            if (s->A[fr[a]][fc[a]]) continue;
             s->R[fr[a]][fc[a]] = p->quantize_inloop ? nearbyint(xhat[a]) : xhat[a];
             s->A[fr[a]][fc[a]] = 1;
         }
@@ -612,34 +639,23 @@ static void scratch_free(oracle_scratch* s) {
     free(s);
 }
 
-/*
- * Conceal every lost block of one frame.
- *   frame: H rows of `pitch` bytes; mb_lost: ceil(H/16) x ceil(W/16) flags (1 = lost).
- *   select: NULL, or per-block flags restricting the work to the selected lost blocks
- *           and the lost blocks they depend on (for sampled checks of large frames).
- *   out: W*H doubles; received pixels are copied, lost pixels of skipped blocks are NaN.
- *   trace: NULL or n_lost*64 records, indexed by raster rank among lost blocks.
- * Returns 0, or -1 on bad arguments (odd sizes).
- */
-int oracle_conceal(const uint8_t* frame, int W, int H, int pitch, const uint8_t* mb_lost,
-                   const uint8_t* select, const oracle_params* p, double* out,
-                   oracle_trace_rec* trace, oracle_stats* stats, int nthreads) {
-    if (W <= 0 || H <= 0 || (W & 1) || (H & 1) || pitch < W || p->ring_step < 1) return -1;
-    if (p->beta_kmax < p->beta_kmin || p->beta_kmax - p->beta_kmin >= 64) return -1;
+static int conceal_frame(const uint8_t* frame, int W, int H, int pitch, const uint8_t* mb_lost,
+                         const uint8_t* px_lost, int px_pitch, const uint8_t* select,
+                         const oracle_params* p, double* out, oracle_trace_rec* trace,
+                         oracle_stats* stats, int nthreads) {
     const int mbw = (W + OR_MB - 1) / OR_MB, mbh = (H + OR_MB - 1) / OR_MB;
     oracle_job job;
     memset(&job, 0, sizeof(job));
     job.frame = frame; job.W = W; job.H = H; job.pitch = pitch;
     job.mb_lost = mb_lost; job.mbw = mbw; job.mbh = mbh; job.p = p;
+    job.px_lost = px_lost; job.px_pitch = px_pitch;
     job.out = out; job.trace = trace;
     job.lost_index = (int32_t*)malloc(sizeof(int32_t) * (size_t)mbw * mbh);
     int nlost = 0;
     for (int b = 0; b < mbw * mbh; b++) job.lost_index[b] = mb_lost[b] ? nlost++ : -1;
     for (int y = 0; y < H; y++)
-        for (int x = 0; x < W; x++) {
-            int b = (y / OR_MB) * mbw + x / OR_MB;
-            out[(size_t)y * W + x] = mb_lost[b] ? NAN : (double)frame[(size_t)y * pitch + x];
-        }
+        for (int x = 0; x < W; x++)
+            out[(size_t)y * W + x] = pixel_lost(&job, y, x) ? NAN : (double)frame[(size_t)y * pitch + x];
     /* which blocks to run: all lost, or the selected ones plus their ancestors */
     unsigned char* run = (unsigned char*)calloc((size_t)mbw * mbh, 1);
     for (int b = mbw * mbh - 1; b >= 0; b--) {
@@ -721,6 +737,49 @@ int oracle_conceal(const uint8_t* frame, int W, int H, int pitch, const uint8_t*
     free(run);
     free(job.lost_index);
     return 0;
+}
+
+static int bad_args(int W, int H, int pitch, const oracle_params* p) {
+    if (W <= 0 || H <= 0 || (W & 1) || (H & 1) || pitch < W || p->ring_step < 1) return 1;
+    if (p->beta_kmax < p->beta_kmin || p->beta_kmax - p->beta_kmin >= 64) return 1;
+    return 0;
+}
+
+/*
+ * Conceal every lost block of one frame.
+ *   frame: H rows of `pitch` bytes; mb_lost: ceil(H/16) x ceil(W/16) flags (1 = lost).
+ *   select: NULL, or per-block flags restricting the work to the selected lost blocks
+ *           and the lost blocks they depend on (for sampled checks of large frames).
+ *   out: W*H doubles; received pixels are copied, lost pixels of skipped blocks are NaN.
+ *   trace: NULL or n_lost*64 records, indexed by raster rank among lost blocks.
+ * Returns 0, or -1 on bad arguments (odd sizes).
+ */
+int oracle_conceal(const uint8_t* frame, int W, int H, int pitch, const uint8_t* mb_lost,
+                   const uint8_t* select, const oracle_params* p, double* out,
+                   oracle_trace_rec* trace, oracle_stats* stats, int nthreads) {
+    if (bad_args(W, H, pitch, p)) return -1;
+    return conceal_frame(frame, W, H, pitch, mb_lost, NULL, 0, select, p, out, trace, stats,
+                         nthreads);
+}
+
+/*
+ * The same for an arbitrarily shaped loss (R9).
+ *   px_lost: H rows of `px_pitch` flags (1 = lost).  The blocks worked on are those holding
+ *   a lost pixel; select, trace and the record index refer to those blocks.
+ */
+int oracle_conceal_px(const uint8_t* frame, int W, int H, int pitch, const uint8_t* px_lost,
+                      int px_pitch, const uint8_t* select, const oracle_params* p, double* out,
+                      oracle_trace_rec* trace, oracle_stats* stats, int nthreads) {
+    if (bad_args(W, H, pitch, p) || px_pitch < W) return -1;
+    const int mbw = (W + OR_MB - 1) / OR_MB, mbh = (H + OR_MB - 1) / OR_MB;
+    uint8_t* mb_lost = (uint8_t*)calloc((size_t)mbw * mbh, 1);
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++)
+            if (px_lost[(size_t)y * px_pitch + x]) mb_lost[(y / OR_MB) * mbw + x / OR_MB] = 1;
+    int rc = conceal_frame(frame, W, H, pitch, mb_lost, px_lost, px_pitch, select, p, out, trace,
+                           stats, nthreads);
+    free(mb_lost);
+    return rc;
 }
 
 int oracle_trace_rec_size(void) { return (int)sizeof(oracle_trace_rec); }

@@ -139,6 +139,54 @@ def loss_mixed(width: int, height: int, seed: int, rate_lo: float, rate_hi: floa
     return flat.reshape(r, c)
 
 
+def loss_shapes(width: int, height: int, seed: int, target: float = 0.10) -> np.ndarray:
+    """Arbitrarily shaped loss, per pixel (uint8 [height, width], 1 = lost): filled ellipses
+    (semi-axes U[2, 20] px, random orientation) and straight strokes (width U{1..6} px,
+    length U[16, 160] px, random direction), half of the shapes each, at uniform random
+    positions, until at least ``target`` of the pixels are lost.  Shapes may overlap and
+    cross block borders; odd widths and offsets leave 2x2 patches partly lost."""
+    rng = np.random.default_rng(seed)
+    m = np.zeros((height, width), dtype=bool)
+    need = int(np.ceil(target * width * height))
+    while int(m.sum()) < need:
+        cy, cx = rng.uniform(0, height), rng.uniform(0, width)
+        th = rng.uniform(0, np.pi)
+        ct, st = np.cos(th), np.sin(th)
+        if rng.uniform() < 0.5:
+            a, b = rng.uniform(2, 20), rng.uniform(2, 20)
+            r = int(np.ceil(max(a, b))) + 1
+            half_u, half_v = a, b
+            ellipse = True
+        else:
+            ln, wd = rng.uniform(16, 160), int(rng.integers(1, 7))
+            r = int(np.ceil(ln / 2 + wd)) + 1
+            half_u, half_v = ln / 2, wd / 2
+            ellipse = False
+        y0, y1 = max(0, int(cy) - r), min(height, int(cy) + r + 1)
+        x0, x1 = max(0, int(cx) - r), min(width, int(cx) + r + 1)
+        if y0 >= y1 or x0 >= x1:
+            continue
+        yy, xx = np.mgrid[y0:y1, x0:x1].astype(np.float64)
+        u = (xx + 0.5 - cx) * ct + (yy + 0.5 - cy) * st
+        v = -(xx + 0.5 - cx) * st + (yy + 0.5 - cy) * ct
+        if ellipse:
+            inside = (u / half_u) ** 2 + (v / half_v) ** 2 <= 1.0
+        else:
+            inside = (np.abs(u) <= half_u) & (np.abs(v) <= half_v)
+        m[y0:y1, x0:x1] |= inside
+    return m.astype(np.uint8)
+
+
+def blocks_of(px_lost: np.ndarray) -> np.ndarray:
+    """Block flags of a per-pixel loss mask: 1 where the 16x16 block holds a lost pixel."""
+    px = np.asarray(px_lost) != 0
+    h, w = px.shape
+    r, c = mb_grid(w, h)
+    pad = np.zeros((r * MB, c * MB), dtype=bool)
+    pad[:h, :w] = px
+    return pad.reshape(r, MB, c, MB).any(axis=(1, 3)).astype(np.uint8)
+
+
 # --------------------------------------------------------------------------------------
 # the five workloads (sizes as stated in the design document)
 
@@ -158,6 +206,13 @@ def workload_slice_1080p(seed: int = 0):
     """1920x1080 with fine texture, runs of 4-20 blocks to >= 20 % loss."""
     f = make_frame(1920, 1080, seed, fine_texture=True)
     return f, loss_runs(1920, 1080, seed + 7, 0.20)
+
+
+def workload_shapes_1080p(seed: int = 0, target: float = 0.10):
+    """1920x1080 with fine texture; arbitrarily shaped loss (ellipses and strokes) to
+    >= ``target`` of the pixels.  Returns (frame, per-pixel mask)."""
+    f = make_frame(1920, 1080, seed, fine_texture=True)
+    return f, loss_shapes(1920, 1080, seed + 11, target)
 
 
 BATCH_SIZES = [(352, 288)] * 24 + [(1280, 720)] * 24 + [(1920, 1080)] * 16

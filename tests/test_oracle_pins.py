@@ -264,7 +264,8 @@ def numpy_hql(R, A, pr, pc, p):
     """Independent NumPy statement of one HQL estimate (Eqs. (3)-(13), readings R5/R7)
     for the patch with top-left (pr, pc) of a 48x48 region R with availability A."""
     wr, wc = pr - 2, pc - 2
-    cfg = [(r, c) for r in range(6) for c in range(6) if A[wr + r, wc + c]]
+    cfg = [(r, c) for r in range(6) for c in range(6)
+           if A[wr + r, wc + c] and not (r in (2, 3) and c in (2, 3))]
     y0 = np.array([R[wr + r, wc + c] for r, c in cfg])
     xcfg = [(2, 2), (2, 3), (3, 2), (3, 3)]
     cands = brute_candidates(A, cfg + xcfg)
@@ -353,3 +354,115 @@ def test_quantize_inloop_is_a_no_op_when_estimates_are_integers():
     b = oracle.conceal(f, m, oracle.params("efficient", quantize_inloop=1, **kw), trace=True)
     assert np.array_equal(a["out"], b["out"])
     assert np.array_equal(a["trace"]["layer"], b["trace"]["layer"])
+
+
+# ---------------------------------------------------------------------------------------
+# Arbitrarily shaped loss (R9: per-pixel mask; the paper notes the method extends to any
+# loss shape)
+
+def shapes_case(seed=0, w=128, h=96, target=0.08):
+    f = synth.make_frame(w, h, seed, fine_texture=True)
+    return f, synth.loss_shapes(w, h, seed + 1, target)
+
+
+@pytest.mark.parametrize("profile", ["efficient", "excellent"])
+def test_pixel_mask_of_whole_blocks_is_the_block_method(profile):
+    # a per-pixel mask that loses whole blocks must give the block method, bit for bit
+    f = synth.make_frame(160, 128, 41, fine_texture=True)
+    m = synth.loss_runs(160, 128, 42, 0.3)
+    a = oracle.conceal(f, m, oracle.params(profile), trace=True)
+    b = oracle.conceal(f, None, oracle.params(profile), px_lost=synth.lost_pixel_mask(m, 160, 128),
+                       trace=True)
+    assert np.array_equal(a["out"], b["out"])
+    assert a["trace"].tobytes() == b["trace"].tobytes()
+    assert a["stats"] == b["stats"]
+
+
+def test_shapes_received_unchanged_lost_inputs_ignored():
+    f, px = shapes_case(3)
+    lost = px.astype(bool)
+    r1 = oracle.conceal(f, None, px_lost=px)
+    assert not np.isnan(r1["out"]).any()
+    assert np.array_equal(r1["out"][~lost], f[~lost].astype(np.float64))
+    g = f.copy()
+    g[lost] = np.random.default_rng(1).integers(0, 256, size=lost.sum())
+    r2 = oracle.conceal(g, None, px_lost=px)
+    assert np.array_equal(r1["out"], r2["out"])
+
+
+@pytest.mark.parametrize("mode", ["efficient", "force_idl", "force_hql"])
+def test_shapes_constant_frame_conceals_to_constant(mode):
+    _, px = shapes_case(5, 96, 96, 0.15)
+    f = np.full((96, 96), 91, np.uint8)
+    kw = {"force_idl": dict(t_phi=-1.0, t_nu=1e-300), "force_hql": dict(t_phi=-1.0, t_nu=1e300)}
+    r = oracle.conceal(f, None, oracle.params("efficient", **kw.get(mode, {})), px_lost=px)
+    assert np.all(np.abs(r["out"] - 91.0) < 1e-9)
+
+
+def test_shapes_intensity_shift_equivariance():
+    f, px = shapes_case(7)
+    f = (30 + (f.astype(np.int32) * 170) // 255).astype(np.uint8)  # [30, 200]
+    a = oracle.conceal(f, None, px_lost=px, trace=True)
+    b = oracle.conceal((f + 40).astype(np.uint8), None, px_lost=px, trace=True)
+    lost = px.astype(bool)
+    assert np.max(np.abs(b["out"][lost] - a["out"][lost] - 40.0)) < 1e-6
+    assert np.array_equal(a["trace"]["layer"], b["trace"]["layer"])
+
+
+def test_shapes_fill_exactly_the_patches_holding_a_lost_pixel():
+    f, px = shapes_case(9)
+    r = oracle.conceal(f, None, px_lost=px, trace=True)
+    blocks = synth.blocks_of(px)
+    ys, xs = np.nonzero(blocks)
+    assert len(r["trace"]) == len(ys)
+    for rank, (by, bx) in enumerate(zip(ys, xs)):
+        sub = px[by * 16:by * 16 + 16, bx * 16:bx * 16 + 16]
+        want = {a * 8 + b for a in range(8) for b in range(8)
+                if sub[2 * a:2 * a + 2, 2 * b:2 * b + 2].any()}
+        recs = r["trace"][rank][:len(want)]
+        assert set(int(p) for p in recs["patch"]) == want
+        assert all(int(m) == by * blocks.shape[1] + bx for m in recs["mb"])
+        assert (r["trace"][rank][len(want):]["ny"] == 0).all()  # no further records
+
+
+def single_lost_pixel(seed, y=50, x=51):
+    f = synth.make_frame(128, 128, seed, fine_texture=True)
+    px = np.zeros((128, 128), np.uint8)
+    px[y, x] = 1
+    return f, px
+
+
+def test_partly_lost_patch_brl_is_mean_of_context_outside_the_patch():
+    # pixel (50, 51) lies in patch (1, 1) of block (3, 3) (rows 50-51, cols 50-51); its
+    # context is the 6x6 window rows 48-53, cols 48-53 less the patch: 32 received pixels;
+    # the patch's three received pixels are not context and stay as they are
+    f, px = single_lost_pixel(4)
+    r = oracle.conceal(f, None, oracle.params("efficient", t_phi=1e9), px_lost=px, trace=True)
+    t = r["trace"][0]
+    assert t[0]["patch"] == 9 and t[0]["ny"] == 32 and t[0]["layer"] == oracle.BRL
+    win = f[48:54, 48:54].astype(np.float64).copy()
+    win[2:4, 2:4] = np.nan
+    assert abs(t[0]["x"][1] - np.nanmean(win)) < 1e-12
+    assert r["out"][50, 51] == t[0]["x"][1]
+    for yy, xx in ((50, 50), (51, 50), (51, 51)):
+        assert r["out"][yy, xx] == f[yy, xx]
+    assert t[1]["ny"] == 0  # one patch only
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_single_lost_pixel_hql_matches_numpy_brute_force(seed):
+    # candidates (R5 with R9): every window of the 48x48 region of block (3, 3) whose 36
+    # positions avoid the one lost pixel; context: the 32 pixels around the patch
+    f, px = single_lost_pixel(seed)
+    p = oracle.params("efficient", t_phi=-1.0, t_nu=1e300)
+    r = oracle.conceal(f, None, p, px_lost=px, trace=True)
+    t0 = r["trace"][0, 0]
+    R = f[32:80, 32:80].astype(np.float64)
+    A = np.ones((48, 48), bool)
+    A[50 - 32, 51 - 32] = False
+    xhat, a_cf, a_scan, bi, M = numpy_hql(R, A, 18, 18, p)
+    assert M == 43 * 43 - 36  # the windows that contain the lost pixel
+    assert t0["layer"] == oracle.HQL and t0["ny"] == 32 and t0["m"] == M and t0["beta_idx"] == bi
+    assert abs(a_cf - t0["alpha"]) < 1e-9
+    assert np.max(np.abs(np.clip(xhat, 0, 255) - t0["x"])) < 1e-8
+    assert r["out"][50, 51] == t0["x"][1]

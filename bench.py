@@ -154,6 +154,7 @@ WORKLOADS = {
     "slice1080p": "1920x1080_runs4-20_20pct_fine_texture",
     "checkerboard": "512x512_checkerboard_25pct",
     "single": "256x256_one_block",
+    "shapes1080p": "1920x1080_shaped_loss_10pct_pixels_ellipses_strokes_fine_texture",
 }
 
 
@@ -162,8 +163,17 @@ def build_workload(seed: int, name: str = "batch"):
     if name == "batch":
         return synth.workload_batch(seed)
     f, m = {"slice1080p": synth.workload_slice_1080p, "checkerboard": synth.workload_checkerboard,
-            "single": synth.workload_single}[name](seed)
+            "single": synth.workload_single, "shapes1080p": synth.workload_shapes_1080p}[name](seed)
     return [f], [m]
+
+
+def lost_blocks(frame, mask) -> int:
+    """Blocks the call works on: lost blocks, or blocks holding a lost pixel of a
+    per-pixel mask (a mask of the frame's own shape)."""
+    from paper_2205_11226_gb300 import synth
+    if mask.shape == frame.shape:
+        return int(synth.blocks_of(mask).sum())
+    return int(mask.sum())
 
 
 def oracle_params_like(p):
@@ -370,7 +380,8 @@ def run_ours(args):
     md = [torch.from_numpy(m).cuda() for m in masks]
     od = [torch.empty_like(f) for f in fd]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
-    n_lost = sum(int(m.sum()) for m in masks)
+    n_lost = sum(lost_blocks(f, m) for f, m in zip(frames, masks))
+    any_px = any(m.shape == f.shape for f, m in zip(frames, masks))
 
     tuned = None
     if not args.no_autotune:  # persistent CTAs per SM, picked by timing this batch
@@ -472,12 +483,17 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "single"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": 4 * args.steps,
+            # per step: block flags of per-pixel masks (if any), queue heights, offsets, fill,
+            # the persistent concealment kernel
+            "gpu_launches": (5 if any_px else 4) * args.steps,
             "roofline": roofline,
             "rooflines_other": other_rooflines,
             "layers": {k: st[k] for k in ("n_patches", "n_brl", "n_idl", "n_hql", "n_brl_nocand")},
             "wall_s_timed": t_wall,
             "clocks": clocks}
+    if any_px:  # the blocks counted are those holding a lost pixel
+        line["config"]["lost_pixels_per_step"] = int(sum(int((m != 0).sum()) for m in masks))
+        line["config"]["patches_filled_per_step"] = st["n_patches"]
     if ws == 1 and not args.no_compare and args.workload == "batch":
         line["compare"] = compare_legs(ctx, skmmse, args, frames, masks, fd, md, od, p, mean_ms, flush,
                                        stream)
@@ -499,9 +515,11 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def synth_lost_mask(mb_lost, shape):
+def synth_lost_mask(mask, shape):
     from paper_2205_11226_gb300 import synth
-    return synth.lost_pixel_mask(mb_lost, shape[1], shape[0])
+    if mask.shape == tuple(shape):
+        return mask != 0
+    return synth.lost_pixel_mask(mask, shape[1], shape[0])
 
 
 def oracle_agreement(ctx, skmmse, p, sample):

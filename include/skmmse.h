@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define SKMMSE_ABI_VERSION 1
+#define SKMMSE_ABI_VERSION 2
 
 typedef enum {
     SKMMSE_OK = 0,
@@ -111,9 +111,20 @@ typedef struct {
 
 /* One frame of a batch.  All pointers are device memory.  `out` may equal `frame`
    (in-place).  `out_f32` (nullable) receives unrounded values: every pixel of a lost
-   block in the frame; received pixels are not written.  `trace` (nullable, used with
-   SKMMSE_FLAG_TRACE) holds n_lost*64 skmmse_trace_rec, indexed by
-   [rank of the block among the frame's lost blocks in raster order][fill step]. */
+   block in the frame; pixels outside lost blocks are not written.  `trace` (nullable,
+   used with SKMMSE_FLAG_TRACE) holds n_lost*64 skmmse_trace_rec, indexed by
+   [rank of the block among the frame's lost blocks in raster order][fill step].
+
+   The loss is given by exactly one of two masks (the other NULL):
+   - mb_lost: ceil(height/16) x ceil(width/16) bytes, 1 = the whole 16x16 block is lost
+     (the loss the paper's experiments use);
+   - px_lost: `height` rows of `px_pitch` bytes, 1 = the pixel is lost: an arbitrarily
+     shaped loss (Sec. II notes the method extends to any shape).  A block holding a lost
+     pixel is a lost block (the unit of work, with the same dependencies); received
+     pixels are support wherever they lie; the 2x2 patches holding a lost pixel are
+     filled in the fill order; a patch's own pixels are never context, and only its lost
+     pixels take the estimate, so received pixels leave the call unchanged.  A px_lost
+     that loses whole blocks gives the mb_lost result bit for bit. */
 typedef struct {
     const uint8_t* frame;
     int width, height, pitch;
@@ -123,6 +134,9 @@ typedef struct {
     float* out_f32;
     int out_f32_pitch;  /* in floats */
     void* trace;
+    const uint8_t* px_lost;
+    int px_pitch;       /* in bytes, >= width when px_lost is given */
+    int reserved;       /* 0 */
 } skmmse_frame;
 
 /* Per-patch decision record (SKMMSE_FLAG_TRACE). */
@@ -196,6 +210,14 @@ skmmse_status skmmse_conceal(skmmse_context* ctx, const uint8_t* d_frame, int wi
                              const skmmse_params* p, uint8_t* d_out, int out_pitch,
                              float* d_out_f32, skmmse_stats* h_stats, void* stream);
 
+/* The same for an arbitrarily shaped loss: d_px_lost holds `height` rows of `px_pitch`
+   bytes, 1 = lost pixel (see skmmse_frame.px_lost).  d_out_f32 (nullable): unrounded
+   values of every pixel of the blocks holding a lost pixel (received ones unchanged). */
+skmmse_status skmmse_conceal_px(skmmse_context* ctx, const uint8_t* d_frame, int width,
+                                int height, int pitch, const uint8_t* d_px_lost, int px_pitch,
+                                const skmmse_params* p, uint8_t* d_out, int out_pitch,
+                                float* d_out_f32, skmmse_stats* h_stats, void* stream);
+
 /* Conceal n frames of any sizes in one persistent launch (one work queue over all lost
    blocks of all frames; a block is claimed once its dependencies are done, the block
    heading the longest remaining chain first).  h_frames is a host array of n descriptors
@@ -249,7 +271,8 @@ skmmse_status skmmse_set_ctas_per_sm(skmmse_context* ctx, int ctas_per_sm);
    attributes for that device (make it before any stream capture on that device).  All
    calls share the one array and it keeps the last call's contents: calls that may overlap
    on the GPU (different streams, or host threads without ordering) race; order them on one
-   stream.  Arguments as skmmse_conceal; p->flags must be 0 (no trace).  h_stats (nullable)
+   stream.  Arguments as skmmse_conceal (whole-block loss only); p->flags may hold
+   SKMMSE_FLAG_QUANTIZE only (no trace).  h_stats (nullable)
    makes the call synchronous and returns the counters. */
 skmmse_status skmmse_conceal_noalloc(const uint8_t* d_frame, int width, int height, int pitch,
                                      const uint8_t* d_mb_lost, const skmmse_params* p,

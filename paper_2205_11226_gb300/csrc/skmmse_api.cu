@@ -76,7 +76,9 @@ skmmse_status validate_params(const skmmse_params* p) {
 }
 
 skmmse_status validate_frame(const skmmse_frame& f) {
-    if (!f.frame || !f.mb_lost || !f.out) return SKMMSE_ERR_ARG;
+    if (!f.frame || !f.out) return SKMMSE_ERR_ARG;
+    if ((f.mb_lost != nullptr) == (f.px_lost != nullptr)) return SKMMSE_ERR_ARG;  // one mask
+    if (f.px_lost && f.px_pitch < f.width) return SKMMSE_ERR_SHAPE;
     if (f.width <= 0 || f.height <= 0 || (f.width & 1) || (f.height & 1)) return SKMMSE_ERR_SHAPE;
     if (f.width > 65536 || f.height > 65536) return SKMMSE_ERR_SHAPE;
     if (f.pitch < f.width || f.out_pitch < f.width) return SKMMSE_ERR_SHAPE;
@@ -140,7 +142,8 @@ cudaError_t set_kernel_attributes() {
 struct BatchLayout {
     long long total_mbs = 0, max_mbs = 1;
     size_t o_frames = 0, o_tmaps = 0, o_eom = 0, o_ent = 0, o_done = 0, o_vals = 0, o_hgt = 0,
-           o_bk = 0, o_rem = 0, o_slots = 0, need = 0, stage_bytes = 0;
+           o_bk = 0, o_rem = 0, o_slots = 0, o_mbmask = 0, need = 0, stage_bytes = 0;
+    bool any_px = false;
 };
 
 skmmse_status plan_batch(const skmmse_frame* frames, int n, const skmmse_params* p, BatchLayout* L) {
@@ -153,6 +156,7 @@ skmmse_status plan_batch(const skmmse_frame* frames, int n, const skmmse_params*
         const long long mbw = (frames[i].width + 15) / 16, mbh = (frames[i].height + 15) / 16;
         L->total_mbs += mbw * mbh;
         if (mbw * mbh > L->max_mbs) L->max_mbs = mbw * mbh;
+        if (frames[i].px_lost) L->any_px = true;
     }
     if (L->total_mbs > (1ll << 28)) return SKMMSE_ERR_SHAPE;
     size_t off = 0;
@@ -167,12 +171,16 @@ skmmse_status plan_batch(const skmmse_frame* frames, int n, const skmmse_params*
     L->o_bk = off; off = align_up(off + sizeof(int) * 4 * L->max_mbs, 128);  // off, cnt, head, tail
     L->o_rem = off; off = align_up(off + sizeof(int) * L->total_mbs, 128);
     L->o_slots = off; off = align_up(off + sizeof(int) * L->total_mbs, 128);
+    L->o_mbmask = off; off = align_up(off + (L->any_px ? L->total_mbs : 0), 128);  // derived block flags
     L->need = off;
     return SKMMSE_OK;
 }
 
+// d_arena: the device arena the descriptors will be used with (the block flags derived
+// from a per-pixel mask live there)
 void fill_descriptors(PFN_cuTensorMapEncodeTiled_v12000 encode, const skmmse_frame* frames, int n,
-                      const skmmse_params* p, const BatchLayout& L, unsigned char* host) {
+                      const skmmse_params* p, const BatchLayout& L, unsigned char* host,
+                      unsigned char* d_arena) {
     FrameDev* hf = reinterpret_cast<FrameDev*>(host + L.o_frames);
     CUtensorMap* ht = reinterpret_cast<CUtensorMap*>(host + L.o_tmaps);
     long long mb_base = 0;
@@ -183,7 +191,9 @@ void fill_descriptors(PFN_cuTensorMapEncodeTiled_v12000 encode, const skmmse_fra
         d.in = f.frame;
         d.out = f.out;
         d.out_f32 = f.out_f32;
-        d.lost = f.mb_lost;
+        d.lost = f.px_lost ? d_arena + L.o_mbmask + mb_base : f.mb_lost;
+        d.px_lost = f.px_lost;
+        d.px_pitch = f.px_lost ? f.px_pitch : 0;
         d.trace = (p->flags & SKMMSE_FLAG_TRACE) ? f.trace : nullptr;
         d.w = f.width;
         d.h = f.height;
@@ -244,6 +254,10 @@ skmmse_status enqueue_batch(const skmmse_frame* frames, int n, const BatchLayout
     w.rem = reinterpret_cast<int*>(arena + L.o_rem);
     w.slots = reinterpret_cast<int*>(arena + L.o_slots);
     w.nbk = (int)L.max_mbs;
+    if (L.any_px) {  // block flags of the per-pixel masks, before the queue reads them
+        sk::px_block_flags_kernel<<<n, sk::kThreads, 0, stream>>>(w, arena + L.o_mbmask);
+        SK_CHECK(cudaGetLastError());
+    }
     sk::queue_heights_kernel<<<n, sk::kThreads, 0, stream>>>(w, kp.concealed_is_support);
     sk::queue_offsets_kernel<<<1, sk::kThreads, 0, stream>>>(w);
     sk::queue_fill_kernel<<<n, sk::kThreads, 0, stream>>>(w, kp.concealed_is_support);
@@ -472,7 +486,7 @@ skmmse_status skmmse_conceal_batch(skmmse_context* c, const skmmse_frame* frames
         SK_CHECK(cudaEventSynchronize(c->stage_done));
         c->stage_pending = false;
     }
-    fill_descriptors(c->encode, frames, n, p, L, c->h_stage);
+    fill_descriptors(c->encode, frames, n, p, L, c->h_stage, c->d_arena);
     SK_CHECK(cudaMemcpyAsync(c->d_arena, c->h_stage, L.stage_bytes, cudaMemcpyHostToDevice, stream));
     SK_CHECK(cudaEventRecord(c->stage_done, stream));
     c->stage_pending = true;
@@ -517,12 +531,12 @@ skmmse_status skmmse_graph_create(skmmse_context* c, const skmmse_frame* frames,
     skmmse_graph* g = new (std::nothrow) skmmse_graph();
     if (!g) return SKMMSE_ERR_NOMEM;
     std::vector<unsigned char> host(L.stage_bytes);
-    fill_descriptors(c->encode, frames, n, p, L, host.data());
     const KParams kp = make_kparams(p);
     g->nbeta = kp.nbeta;
     const long long grid = (long long)c->sm_count * (c->ctas_per_sm > 0 ? c->ctas_per_sm : c->blocks_per_sm);
     cudaStream_t cs = nullptr;
     cudaError_t e = cudaMalloc(&g->d_arena, L.need);
+    if (e == cudaSuccess) fill_descriptors(c->encode, frames, n, p, L, host.data(), g->d_arena);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_counters, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_stats, sk::kNStats * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpy(g->d_arena, host.data(), L.stage_bytes, cudaMemcpyHostToDevice);
@@ -620,6 +634,25 @@ skmmse_status skmmse_conceal(skmmse_context* c, const uint8_t* d_frame, int widt
     f.height = height;
     f.pitch = pitch;
     f.mb_lost = d_mb_lost;
+    f.out = d_out;
+    f.out_pitch = out_pitch;
+    f.out_f32 = d_out_f32;
+    f.out_f32_pitch = width;
+    return skmmse_conceal_batch(c, &f, 1, p, h_stats, stream);
+}
+
+skmmse_status skmmse_conceal_px(skmmse_context* c, const uint8_t* d_frame, int width, int height,
+                                int pitch, const uint8_t* d_px_lost, int px_pitch,
+                                const skmmse_params* p, uint8_t* d_out, int out_pitch,
+                                float* d_out_f32, skmmse_stats* h_stats, void* stream) {
+    skmmse_frame f;
+    std::memset(&f, 0, sizeof(f));
+    f.frame = d_frame;
+    f.width = width;
+    f.height = height;
+    f.pitch = pitch;
+    f.px_lost = d_px_lost;
+    f.px_pitch = px_pitch;
     f.out = d_out;
     f.out_pitch = out_pitch;
     f.out_f32 = d_out_f32;

@@ -101,13 +101,15 @@ struct FrameDev {
     const uint8_t* in;
     uint8_t* out;
     float* out_f32;
-    const uint8_t* lost;
+    const uint8_t* lost;      // block flags (given, or derived from px_lost)
     void* trace;
+    const uint8_t* px_lost;   // per-pixel loss (arbitrarily shaped), or null: whole blocks
     int w, h, pitch, out_pitch, out_f32_pitch;
     int mbw, mbh;
     int mb_base;  // offset of this frame's blocks in entry_of_mb
     int use_tma;
-    int pad[3];
+    int px_pitch;
+    int pad[2];
 };
 
 struct WorkDev {
@@ -440,9 +442,10 @@ __device__ __forceinline__ int select_patch(const Smem& sm, int lane) {
         if ((uf >> p) & 1ull) {
             const int a = p >> 3, b = p & 7;
             const int wr = kMB + 2 * a - 2, wc = kMB + 2 * b - 2;
-            int cnt = 0;
+            int cnt = 0;  // the 6x6 window less the patch's own four pixels
 #pragma unroll
-            for (int r = 0; r < 6; ++r) cnt += __popc((unsigned)(sm.av[wr + r] >> wc) & 63u);
+            for (int r = 0; r < 6; ++r)
+                cnt += __popc((unsigned)(sm.av[wr + r] >> wc) & ((r == 2 || r == 3) ? 0x33u : 63u));
             best = max(best, cnt * 64 + (63 - p));
         }
     }
@@ -465,7 +468,8 @@ __device__ __forceinline__ CtxStats ctx_stats(const Smem& sm, int wr, int wc, in
     for (int h2 = 0; h2 < 2; ++h2) {  // window position k of this lane: its availability bit
         const int k = lane + 32 * h2;
         const int r = k / 6, c = k - 6 * (k / 6);
-        const bool on = k < 36 && ((sm.av[wr + r] >> (wc + c)) & 1ull);
+        const bool own = (r == 2 || r == 3) && (c == 2 || c == 3);  // the patch: never context
+        const bool on = k < 36 && !own && ((sm.av[wr + r] >> (wc + c)) & 1ull);
         bal[h2] = __ballot_sync(0xffffffffu, on);
         if (on) {
             const float v = sm.S[(wr + r) * kReg + wc + c];
@@ -1979,6 +1983,11 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                         } else if (st == 1) {
                             v = __ldcg(&W.vals[(size_t)sm.nbent[nb] * 256 + (r % kMB) * kMB + cc % kMB]);
                             av = true;
+                        } else if (F.px_lost && F.px_lost[(size_t)fy * F.px_pitch + fx] == 0) {
+                            // a received pixel of a lost block (per-pixel loss)
+                            v = F.use_tma ? (float)sm.raw[r * kReg + cc]
+                                          : (float)F.in[(size_t)fy * F.pitch + fx];
+                            av = true;
                         }
                     }
                     sm.S[r * kReg + cc] = v;
@@ -1988,11 +1997,15 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
             }
             if (lane == 0) sm.av[r] = bits;
         }
-        if (tid == 0) {
+        __syncthreads();
+        if (tid == 0) {  // patches to fill: in the frame, holding a lost (unavailable) pixel
             unsigned long long uf = 0;
             for (int a = 0; a < 8; ++a)
-                for (int b = 0; b < 8; ++b)
-                    if (mby * kMB + 2 * a < F.h && mbx * kMB + 2 * b < F.w) uf |= 1ull << (a * 8 + b);
+                for (int b = 0; b < 8; ++b) {
+                    const int pr = kMB + 2 * a, pc = kMB + 2 * b;
+                    const bool full = ((sm.av[pr] >> pc) & 3ull) == 3ull && ((sm.av[pr + 1] >> pc) & 3ull) == 3ull;
+                    if (mby * kMB + 2 * a < F.h && mbx * kMB + 2 * b < F.w && !full) uf |= 1ull << (a * 8 + b);
+                }
             sm.unfilled = uf;
             sm.st[ST_LOST] += 1;
         }
@@ -2028,8 +2041,10 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                         float xw = fminf(fmaxf(xv, 0.0f), 255.0f);
                         if (force_on && trace_base) xw = trace_base[step].x[lane];  // verification hook
                         if (quant_on) xw = rintf(xw);
-                        sm.S[(pr + (lane >> 1)) * kReg + pc + (lane & 1)] = xw;
+                        const int rr = pr + (lane >> 1), cc = pc + (lane & 1);
+                        if (!((sm.av[rr] >> cc) & 1ull)) sm.S[rr * kReg + cc] = xw;  // lost pixels only
                     }
+                    __syncwarp();
                     if (lane == 0) {
                         sm.av[pr] |= 3ull << pc;
                         sm.av[pr + 1] |= 3ull << pc;
@@ -2079,8 +2094,8 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
             c.wc = kMB + 2 * c.pb - 2;
             c.ymask = 0;
 #pragma unroll
-            for (int r = 0; r < 6; ++r) {
-                const unsigned bits = (unsigned)(sm.av[c.wr + r] >> c.wc) & 63u;
+            for (int r = 0; r < 6; ++r) {  // context: the window less the patch
+                const unsigned bits = (unsigned)(sm.av[c.wr + r] >> c.wc) & ((r == 2 || r == 3) ? 0x33u : 63u);
                 c.ymask |= (unsigned long long)bits << (6 * r);
             }
             c.ny = sm.hand.ny;
@@ -2144,10 +2159,11 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
 #pragma unroll
                     for (int a = 0; a < 4; ++a) xw[a] = rintf(xw[a]);
                 }
-                sm.S[pr * kReg + pc] = xw[0];
-                sm.S[pr * kReg + pc + 1] = xw[1];
-                sm.S[(pr + 1) * kReg + pc] = xw[2];
-                sm.S[(pr + 1) * kReg + pc + 1] = xw[3];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {  // lost pixels only (received ones are available)
+                    const int rr = pr + (a >> 1), cc = pc + (a & 1);
+                    if (!((sm.av[rr] >> cc) & 1ull)) sm.S[rr * kReg + cc] = xw[a];
+                }
                 sm.av[pr] |= 3ull << pc;
                 sm.av[pr + 1] |= 3ull << pc;
                 sm.unfilled &= ~(1ull << (c.pa * 8 + c.pb));
@@ -2200,6 +2216,31 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
     if (tid == 0 && sm.mma_err) atomicExch(&W.counters[2], 6);
     for (int i = tid; i < kNStats; i += kThreads)
         if (sm.st[i]) atomicAdd(&W.stats[i], sm.st[i]);
+}
+
+// ------------------------------------------------------------------------------------
+// Block flags of per-pixel loss masks: a block is lost iff it holds a lost pixel.  One CTA
+// per frame, one warp per block (lane: half a row of the block).  Frames given block flags
+// are skipped.  flags: the derived flags of all frames, at each frame's mb_base.
+__global__ void __launch_bounds__(kThreads) px_block_flags_kernel(const __grid_constant__ WorkDev W,
+                                                                   uint8_t* flags) {
+    const FrameDev& F = W.frames[blockIdx.x];
+    if (!F.px_lost) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nmb = F.mbw * F.mbh;
+    for (int mb = wid; mb < nmb; mb += kWarps) {
+        const int by = mb / F.mbw, bx = mb - by * F.mbw;
+        const int y = by * kMB + (lane >> 1), x0 = bx * kMB + (lane & 1) * 8;
+        bool any = false;
+        if (y < F.h) {
+            const uint8_t* row = F.px_lost + (size_t)y * F.px_pitch;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (x0 + i < F.w && row[x0 + i] != 0) any = true;
+        }
+        const bool lost = __any_sync(0xffffffffu, any);
+        if (lane == 0) flags[F.mb_base + mb] = lost ? 1 : 0;
+    }
 }
 
 // ------------------------------------------------------------------------------------

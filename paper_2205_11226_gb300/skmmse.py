@@ -29,6 +29,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported frame shape", 3: "unsu
           6: "dependency wait timed out on the device", 7: "unsupported precision or flag",
           8: "frame exceeds the static scratch of the no-allocation entry point"}
 NOALLOC_MAX_MBS = 8192
+ABI_VERSION = 2
 
 
 class Params(ctypes.Structure):
@@ -45,7 +46,8 @@ class Frame(ctypes.Structure):
         ("frame", ctypes.c_void_p), ("width", ctypes.c_int), ("height", ctypes.c_int),
         ("pitch", ctypes.c_int), ("mb_lost", ctypes.c_void_p), ("out", ctypes.c_void_p),
         ("out_pitch", ctypes.c_int), ("out_f32", ctypes.c_void_p), ("out_f32_pitch", ctypes.c_int),
-        ("trace", ctypes.c_void_p),
+        ("trace", ctypes.c_void_p), ("px_lost", ctypes.c_void_p), ("px_pitch", ctypes.c_int),
+        ("reserved", ctypes.c_int),
     ]
 
 
@@ -73,7 +75,7 @@ TRACE_DTYPE = np.dtype([
 
 # every symbol include/skmmse.h declares
 EXPORTS = ["skmmse_abi_version", "skmmse_struct_size", "skmmse_status_str", "skmmse_params_preset",
-           "skmmse_create", "skmmse_destroy", "skmmse_conceal", "skmmse_conceal_batch",
+           "skmmse_create", "skmmse_destroy", "skmmse_conceal", "skmmse_conceal_px", "skmmse_conceal_batch",
            "skmmse_read_stats", "skmmse_read_phase_clocks", "skmmse_conceal_noalloc",
            "skmmse_probe_peaks",
            "skmmse_graph_create", "skmmse_graph_launch", "skmmse_graph_read_stats",
@@ -111,6 +113,9 @@ def load(path: str = LIB_PATH):
     lib.skmmse_conceal.restype = ci
     lib.skmmse_conceal.argtypes = [vp, vp, ci, ci, ci, vp, ctypes.POINTER(Params), vp, ci, vp,
                                    ctypes.POINTER(Stats), vp]
+    lib.skmmse_conceal_px.restype = ci
+    lib.skmmse_conceal_px.argtypes = [vp, vp, ci, ci, ci, vp, ci, ctypes.POINTER(Params), vp, ci, vp,
+                                      ctypes.POINTER(Stats), vp]
     lib.skmmse_conceal_batch.restype = ci
     lib.skmmse_conceal_batch.argtypes = [vp, ctypes.POINTER(Frame), ci, ctypes.POINTER(Params),
                                          ctypes.POINTER(Stats), vp]
@@ -137,6 +142,7 @@ def load(path: str = LIB_PATH):
     lib.skmmse_probe_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     lib.skmmse_read_phase_clocks.restype = ci
     lib.skmmse_read_phase_clocks.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), vp]
+    assert lib.skmmse_abi_version() == ABI_VERSION, "library ABI version"
     assert lib.skmmse_struct_size(0) == TRACE_DTYPE.itemsize, "trace record layout"
     assert lib.skmmse_struct_size(1) == ctypes.sizeof(Stats), "stats layout"
     assert lib.skmmse_struct_size(2) == ctypes.sizeof(Params), "params layout"
@@ -196,36 +202,54 @@ class Context:
             pass
 
     # ---------------------------------------------------------------------------------
-    def conceal(self, frame, mb_lost, p: Params | None = None, *, out=None, out_f32=None,
-                stats: bool = False, stream=None):
-        """frame: uint8 CUDA tensor [H, W]; mb_lost: uint8 CUDA tensor [ceil(H/16), ceil(W/16)].
+    def conceal(self, frame, mb_lost, p: Params | None = None, *, px_lost=None, out=None,
+                out_f32=None, stats: bool = False, stream=None):
+        """frame: uint8 CUDA tensor [H, W]; mb_lost: uint8 CUDA tensor [ceil(H/16), ceil(W/16)]
+        (whole lost blocks), or None with px_lost: uint8 CUDA tensor [H, W] (arbitrarily
+        shaped loss, 1 = lost pixel).
         Returns (out, out_f32, stats_dict_or_None); out_f32 only if given (or True)."""
         import torch
         p = p if p is not None else params()
         assert frame.is_cuda and frame.dtype == torch.uint8 and frame.dim() == 2
-        assert mb_lost.is_cuda and mb_lost.dtype == torch.uint8 and mb_lost.is_contiguous()
+        assert (mb_lost is None) != (px_lost is None), "give mb_lost or px_lost"
+        mask = mb_lost if px_lost is None else px_lost
+        assert mask.is_cuda and mask.dtype == torch.uint8 and mask.stride(1) == 1
         H, W = frame.shape
         if out is None:
             out = torch.empty_like(frame)
         if out_f32 is True:
             out_f32 = torch.zeros((H, W), dtype=torch.float32, device=frame.device)
         st = Stats() if stats else None
-        rc = self._lib.skmmse_conceal(
-            self._h, frame.data_ptr(), W, H, frame.stride(0), mb_lost.data_ptr(), ctypes.byref(p),
-            out.data_ptr(), out.stride(0), out_f32.data_ptr() if out_f32 is not None else None,
-            ctypes.byref(st) if st is not None else None, _stream_handle(stream))
-        _check(rc, "skmmse_conceal")
+        tail = (ctypes.byref(p), out.data_ptr(), out.stride(0),
+                out_f32.data_ptr() if out_f32 is not None else None,
+                ctypes.byref(st) if st is not None else None, _stream_handle(stream))
+        if px_lost is None:
+            assert mb_lost.is_contiguous()
+            rc = self._lib.skmmse_conceal(self._h, frame.data_ptr(), W, H, frame.stride(0),
+                                          mb_lost.data_ptr(), *tail)
+        else:
+            assert tuple(px_lost.shape) == (H, W)
+            rc = self._lib.skmmse_conceal_px(self._h, frame.data_ptr(), W, H, frame.stride(0),
+                                             px_lost.data_ptr(), px_lost.stride(0), *tail)
+        _check(rc, "skmmse_conceal" if px_lost is None else "skmmse_conceal_px")
         return out, out_f32, (st.as_dict() if st is not None else None)
 
     @staticmethod
     def _descs(frames, masks, outs, outs_f32=None, traces=None):
+        """masks[i]: block flags [ceil(H/16), ceil(W/16)] (contiguous), or a per-pixel mask
+        of the frame's own shape [H, W] (arbitrarily shaped loss)."""
         n = len(frames)
         descs = (Frame * n)()
         for i, (f, m) in enumerate(zip(frames, masks)):
             H, W = f.shape
             d = descs[i]
             d.frame, d.width, d.height, d.pitch = f.data_ptr(), W, H, f.stride(0)
-            d.mb_lost = m.data_ptr()
+            if tuple(m.shape) == (H, W):
+                assert m.stride(1) == 1
+                d.px_lost, d.px_pitch = m.data_ptr(), m.stride(0)
+            else:
+                assert m.is_contiguous()
+                d.mb_lost = m.data_ptr()
             d.out, d.out_pitch = outs[i].data_ptr(), outs[i].stride(0)
             if outs_f32 is not None and outs_f32[i] is not None:
                 d.out_f32, d.out_f32_pitch = outs_f32[i].data_ptr(), outs_f32[i].stride(0)
@@ -325,10 +349,20 @@ class Graph:
             pass
 
 
-def trace_buffer(mb_lost_np: np.ndarray, device="cuda"):
-    """Device buffer for the per-patch decision records of one frame."""
+def _px_blocks(px: np.ndarray) -> np.ndarray:
+    h, w = px.shape
+    r, c = (h + 15) // 16, (w + 15) // 16
+    pad = np.zeros((r * 16, c * 16), dtype=bool)
+    pad[:h, :w] = px
+    return pad.reshape(r, 16, c, 16).any(axis=(1, 3))
+
+
+def trace_buffer(mask_np: np.ndarray, device="cuda", px: bool = False):
+    """Device buffer for the per-patch decision records of one frame (mask: the block
+    flags, or with px=True the per-pixel mask)."""
     import torch
-    nlost = int((np.asarray(mb_lost_np) != 0).sum())
+    m = np.asarray(mask_np) != 0
+    nlost = int(_px_blocks(m).sum()) if px else int(m.sum())
     return torch.zeros(max(1, nlost) * 64 * TRACE_DTYPE.itemsize, dtype=torch.uint8, device=device)
 
 
@@ -337,33 +371,36 @@ def trace_to_numpy(buf, nlost: int) -> np.ndarray:
     return np.frombuffer(raw, dtype=TRACE_DTYPE).reshape(max(1, nlost), 64)[:nlost]
 
 
-def conceal_numpy(frame: np.ndarray, mb_lost: np.ndarray, p: Params | None = None, *,
-                  trace: bool = False, ctx: Context | None = None, force_x: np.ndarray | None = None):
+def conceal_numpy(frame: np.ndarray, mb_lost: np.ndarray | None, p: Params | None = None, *,
+                  px_lost: np.ndarray | None = None, trace: bool = False,
+                  ctx: Context | None = None, force_x: np.ndarray | None = None):
     """Host-buffer convenience: copy in, conceal on cuda:0, copy out.
+    mb_lost: block flags, or None with px_lost: per-pixel loss [H, W].
     Returns dict(out=uint8 [H, W], out_f32=float32 [H, W], stats, trace).
     force_x (verification hook, float [n_lost, 64, 4]): reference estimates written back
     into the support after each step instead of the kernel's own (SKMMSE_FLAG_FORCE)."""
     import torch
     p = params() if p is None else p
     ctx = ctx or Context()
+    assert (mb_lost is None) != (px_lost is None), "give mb_lost or px_lost"
+    mask = np.ascontiguousarray(np.asarray(mb_lost if px_lost is None else px_lost) != 0, dtype=np.uint8)
+    nlost = int(mask.sum()) if px_lost is None else int(_px_blocks(mask != 0).sum())
     f = torch.from_numpy(np.ascontiguousarray(frame, dtype=np.uint8)).cuda()
-    m = torch.from_numpy(np.ascontiguousarray(mb_lost, dtype=np.uint8)).cuda()
+    m = torch.from_numpy(mask).cuda()
     of = torch.zeros(f.shape, dtype=torch.float32, device=f.device)
     tb = None
     if trace or force_x is not None:
         p = Params.from_buffer_copy(p)
         p.flags |= FLAG_TRACE
-        nlost = int((np.asarray(mb_lost) != 0).sum())
         if force_x is not None:
             p.flags |= FLAG_FORCE
             rec = np.zeros((max(1, nlost), 64), dtype=TRACE_DTYPE)
             rec["x"][:nlost] = np.asarray(force_x, dtype=np.float32).reshape(nlost, 64, 4)
             tb = torch.from_numpy(rec.view(np.uint8).reshape(-1).copy()).cuda()
         else:
-            tb = trace_buffer(mb_lost)
+            tb = trace_buffer(mask, px=px_lost is not None)
     outs, st = ctx.conceal_batch([f], [m], p, outs_f32=[of], traces=[tb] if tb is not None else None,
                                  stats=True)
     torch.cuda.synchronize()
-    nlost = int((mb_lost != 0).sum())
     return {"out": outs[0].cpu().numpy(), "out_f32": of.cpu().numpy(), "stats": st,
             "trace": trace_to_numpy(tb, nlost) if tb is not None else None}

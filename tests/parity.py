@@ -16,13 +16,16 @@ In both, decisions (BRL/IDL/HQL, IDL ring, beta*, I0) are taken by thresholds an
 on floating-point values; a difference is accepted only where the oracle's own margin for
 that decision is below a near-tie bound.  The fill order (availability only) and the
 context sizes must always be identical.
+
+A loss mask is either block flags [ceil(H/16), ceil(W/16)] or a per-pixel mask of the
+frame's shape (arbitrarily shaped loss); every helper takes both.
 """
 from __future__ import annotations
 
 import numpy as np
 
 import oracle
-from paper_2205_11226_gb300 import skmmse
+from paper_2205_11226_gb300 import skmmse, synth
 
 TOL_FP32 = 1e-3          # gray levels per pixel (FP32 path)
 NEAR_TIE = {"phi": 1e-3, "nu": 1e-3, "beta": 1e-3, "i0": 1e-3}
@@ -38,8 +41,34 @@ def matching_oracle_params(p: skmmse.Params, store_f32: int = 0) -> oracle.Param
                          quantize_inloop=1 if (p.flags & skmmse.FLAG_QUANTIZE) else 0)
 
 
-def in_frame_patches(by, bx, W, H):
-    return sum(1 for a in range(8) for b in range(8) if by * 16 + 2 * a < H and bx * 16 + 2 * b < W)
+def loss_views(frame, mask):
+    """(block flags, lost-pixel mask, per_pixel) of a block or per-pixel loss mask."""
+    H, W = frame.shape
+    m = np.asarray(mask) != 0
+    if m.shape == (H, W):
+        return synth.blocks_of(m).astype(bool), m, True
+    return m, synth.lost_pixel_mask(m, W, H), False
+
+
+def patches_to_fill(lostpx, by, bx):
+    """Patches of block (by, bx) holding a lost pixel (all in-frame ones for a lost block)."""
+    sub = lostpx[by * 16:by * 16 + 16, bx * 16:bx * 16 + 16]
+    return sum(1 for a in range(0, sub.shape[0], 2) for b in range(0, sub.shape[1], 2)
+               if sub[a:a + 2, b:b + 2].any())
+
+
+def oracle_conceal(frame, mask, op, **kw):
+    blocks, lostpx, px = loss_views(frame, mask)
+    if px:
+        return oracle.conceal(frame, None, op, px_lost=lostpx, **kw)
+    return oracle.conceal(frame, mask, op, **kw)
+
+
+def gpu_conceal(frame, mask, p, **kw):
+    blocks, lostpx, px = loss_views(frame, mask)
+    if px:
+        return skmmse.conceal_numpy(frame, None, p, px_lost=lostpx, **kw)
+    return skmmse.conceal_numpy(frame, mask, p, **kw)
 
 
 def compare(frame, mb_lost, gpu, orc, p: skmmse.Params, tol=TOL_FP32, forced=False, near_tie=1.0):
@@ -48,6 +77,7 @@ def compare(frame, mb_lost, gpu, orc, p: skmmse.Params, tol=TOL_FP32, forced=Fal
     before the first decision difference of a block).  near_tie scales the near-tie
     bounds (free-running mixed precision drifts further from the oracle's inputs)."""
     H, W = frame.shape
+    mb_lost, lostpx, _ = loss_views(frame, mb_lost)
     mbh, mbw = mb_lost.shape
     lost = [(y, x) for y in range(mbh) for x in range(mbw) if mb_lost[y, x]]
     gtr, otr = gpu["trace"], orc["trace"]
@@ -62,7 +92,7 @@ def compare(frame, mb_lost, gpu, orc, p: skmmse.Params, tol=TOL_FP32, forced=Fal
             if any(d in tainted for d in deps):
                 tainted.add(b)
                 continue
-        npatch = in_frame_patches(by, bx, W, H)
+        npatch = patches_to_fill(lostpx, by, bx)
         rep["patches"] += npatch
         flipped = False
         for s in range(npatch):
@@ -113,33 +143,31 @@ def compare(frame, mb_lost, gpu, orc, p: skmmse.Params, tol=TOL_FP32, forced=Fal
             rep["blocks_compared"] += 1
     rep["tainted_blocks"] = len(tainted)
     # received pixels untouched
-    recv = ~np.kron(mb_lost.astype(bool), np.ones((16, 16), bool))[:H, :W]
+    recv = ~lostpx
     assert np.array_equal(gpu["out"][recv], frame[recv])
     return rep
 
 
 def run_pair(frame, mb_lost, p: skmmse.Params, ctx=None, threads=8):
     """Free-running pair: kernel and FP64 oracle independently."""
-    gpu = skmmse.conceal_numpy(frame, mb_lost, p, trace=True, ctx=ctx)
-    orc = oracle.conceal(frame, mb_lost, matching_oracle_params(p), trace=True, threads=threads)
+    gpu = gpu_conceal(frame, mb_lost, p, trace=True, ctx=ctx)
+    orc = oracle_conceal(frame, mb_lost, matching_oracle_params(p), trace=True, threads=threads)
     return gpu, orc
 
 
 def run_forced(frame, mb_lost, p: skmmse.Params, ctx=None, threads=8):
     """Teacher-forced pair: the oracle stores binary32 estimates; the kernel writes those
     back after each step, so both see identical inputs at every step."""
-    orc = oracle.conceal(frame, mb_lost, matching_oracle_params(p, store_f32=1), trace=True,
+    orc = oracle_conceal(frame, mb_lost, matching_oracle_params(p, store_f32=1), trace=True,
                          threads=threads)
-    nl = int((np.asarray(mb_lost) != 0).sum())
-    gpu = skmmse.conceal_numpy(frame, mb_lost, p, ctx=ctx, force_x=orc["trace"]["x"][:nl])
+    nl = int(loss_views(frame, mb_lost)[0].sum())
+    gpu = gpu_conceal(frame, mb_lost, p, ctx=ctx, force_x=orc["trace"]["x"][:nl])
     return gpu, orc
 
 
 def free_running_summary(frame, mb_lost, gpu, orc):
     """Error statistics of a free-running pair over the lost pixels."""
-    from paper_2205_11226_gb300 import synth
-    H, W = frame.shape
-    lost = synth.lost_pixel_mask(mb_lost, W, H)
+    lost = loss_views(frame, mb_lost)[1]
     d = np.abs(gpu["out_f32"].astype(np.float64) - orc["out"])[lost]
     ref_q = np.clip(np.rint(orc["out"]), 0, 255).astype(np.uint8)
     return {"max_err": float(d.max()) if d.size else 0.0,
@@ -153,19 +181,18 @@ def assembled_psnr_delta(frame, mb_lost, gpu, orc):
     """|PSNR(gpu) - PSNR(oracle)| over the lost pixels of the frames assembled from the two
     sets of per-step estimates (trace x, rounded to 8 bits).  With a teacher-forced pair
     this measures the arithmetic of the path alone: every step had the oracle's inputs."""
-    from paper_2205_11226_gb300 import synth
     H, W = frame.shape
+    mb_lost, lm, _ = loss_views(frame, mb_lost)
     mbh, mbw = mb_lost.shape
     lost = [(y, x) for y in range(mbh) for x in range(mbw) if mb_lost[y, x]]
     out = {}
     for name, tr in (("gpu", gpu["trace"]), ("orc", orc["trace"])):
         a = np.full((H, W), np.nan)
         for rank, (by, bx) in enumerate(lost):
-            for s in range(in_frame_patches(by, bx, W, H)):
+            for s in range(patches_to_fill(lm, by, bx)):
                 rec = tr[rank, s]
                 pa, pb = int(rec["patch"]) >> 3, int(rec["patch"]) & 7
                 y, x = by * 16 + 2 * pa, bx * 16 + 2 * pb
                 a[y:y + 2, x:x + 2] = np.asarray(rec["x"], np.float64).reshape(2, 2)
         out[name] = np.clip(np.rint(a), 0, 255)
-    lm = synth.lost_pixel_mask(mb_lost, W, H)
     return abs(synth.psnr(out["gpu"], frame, lm) - synth.psnr(out["orc"], frame, lm))

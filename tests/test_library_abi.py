@@ -32,7 +32,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_struct_layouts(lib):
-    assert lib.skmmse_abi_version() == 1
+    assert lib.skmmse_abi_version() == 2
     assert lib.skmmse_struct_size(0) == skmmse.TRACE_DTYPE.itemsize == 120
     assert lib.skmmse_struct_size(1) == ctypes.sizeof(skmmse.Stats)
     assert lib.skmmse_struct_size(2) == ctypes.sizeof(skmmse.Params)

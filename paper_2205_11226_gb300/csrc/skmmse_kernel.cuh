@@ -203,12 +203,7 @@ struct __align__(16) Hql {
                 HqlP2 p2;
             };
         };
-        struct {  // tensor-core operand tiles: 128 rows x 64 16-bit columns, K-major, no swizzle
-            __align__(16) uint16_t t0[128 * 64];
-            __align__(16) uint16_t t1[128 * 64];
-            __align__(16) uint16_t t2[128 * 64];
-            __align__(16) uint16_t t3[128 * 64];
-        } mx;
+        __align__(16) uint16_t mx[32768];  // tensor-core operand tiles (64 KB; layout in tl::)
     };
 };
 
@@ -798,9 +793,40 @@ __device__ __forceinline__ void store8_int_frac(uint16_t* tn, uint16_t* tfh, uin
     *reinterpret_cast<uint4*>(tfl + off) = make_uint4(fl[0], fl[1], fl[2], fl[3]);
 }
 
-__device__ __forceinline__ void zero_tiles(Hql& h) {
-    uint4* p = reinterpret_cast<uint4*>(&h.mx);
-    for (int i = threadIdx.x; i < (int)(sizeof(h.mx) / 16); i += kThreads) p[i] = make_uint4(0, 0, 0, 0);
+// Operand tiles of the tensor-core passes in the 64 KB region h.mx (byte offsets), two
+// buffers per pass: the MMAs of one chunk run while the next chunk is staged.  The MMAs
+// are M = 64 (A rows), N = 32 or 48 (B rows): the tensor cores read their operands from
+// shared memory for every MMA, and that traffic (not the arithmetic) sets their time, so
+// the shapes stay as close to the live rows as the instruction allows.  A tile holds only
+// its live rows (K-major, no swizzle: 8-row groups of K/8 core matrices, 128 B each).  An
+// A descriptor reads 64 rows from the tile start; the rows past a shorter tile hold other
+// data of the region and only produce rows of D that are never read.  Every such read
+// window ends inside the region.
+namespace tl {
+constexpr uint32_t kRegion = 65536;
+constexpr uint32_t kWinK64 = 64 * 64 * 2;  // bytes an M = 64, K = 64 A descriptor reads
+constexpr uint32_t kWinK32 = 64 * 32 * 2;  // M = 64, K = 32
+// H1, K = 64: integer part, fraction high and low halves (48 rows: features, the constant
+// in row 36); then the int32 sums
+constexpr uint32_t kH1Tile = 48 * 64 * 2, kH1Buf = 3 * kH1Tile, kH1Sums = 49152;
+constexpr uint32_t kH1SumsBytes = 36 * 40 * 4;
+// H2, K = 32: A = candidates (64 rows) high / low; B = L^-1 (32 rows) high / low
+constexpr uint32_t kH2A = 4096, kH2ABuf = 2 * kH2A, kH2B = 16384, kH2BTile = 2048;
+// H3, K = 64: A = weights (32 rows: beta) high / low; B = Z' (48 rows) high / low
+constexpr uint32_t kH3W = 4096, kH3WBuf = 2 * kH3W, kH3Z = 16384, kH3ZTile = 6144, kH3ZBuf = 2 * kH3ZTile;
+static_assert(kH1Buf + 2 * kH1Tile + kWinK64 <= kRegion && 2 * kH1Buf <= kH1Sums &&
+                  kH1Sums + kH1SumsBytes <= kRegion, "H1 tiles");
+static_assert(kH2ABuf + kH2A + kWinK32 <= kRegion && 2 * kH2ABuf <= kH2B && kH2B + 2 * kH2BTile <= kRegion,
+              "H2 tiles");
+static_assert(kH3WBuf + kH3W + kWinK64 <= kRegion && 2 * kH3WBuf <= kH3Z && kH3Z + 2 * kH3ZBuf <= kRegion,
+              "H3 tiles");
+}  // namespace tl
+
+__device__ __forceinline__ uint16_t* tile(Hql& h, uint32_t byte_off) { return h.mx + (byte_off >> 1); }
+
+__device__ __forceinline__ void zero_region(Hql& h, uint32_t off, uint32_t bytes) {
+    uint4* p = reinterpret_cast<uint4*>(tile(h, off));
+    for (int i = threadIdx.x; i < (int)(bytes / 16); i += kThreads) p[i] = make_uint4(0, 0, 0, 0);
 }
 
 // D (+)= A * B^T over K columns with split operands (issued by one thread)
@@ -819,17 +845,29 @@ __device__ __forceinline__ void mma3(uint32_t tmem, const uint16_t* ahi, const u
     }
 }
 
-// make the staged tiles visible to the tensor cores, issue (thread 0), wait for completion
-template <typename IssueF>
-__device__ __forceinline__ void mma_round(Smem& sm, uint32_t& mph, IssueF issue) {
+// The chunk pipeline of a pass: [tiles_ready] issue the MMAs of chunk c, stage chunk c + 1
+// into the other buffer, [mma_wait] chunk c complete.  Issuing an MMA stalls the issuing
+// thread until the tensor core takes it; the issuer is lane 0 of the last warp, whose
+// threads take one staging task each (the second round of tasks goes to the first warps).
+constexpr int kIssuer = kThreads - 32;
+// Staged tiles visible to the tensor cores; every thread past the previous chunk's
+// tensor-memory reads.
+__device__ __forceinline__ void tiles_ready() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (threadIdx.x == 0) {
+}
+
+template <typename IssueF>
+__device__ __forceinline__ void mma_issue(Smem& sm, IssueF issue) {
+    if (threadIdx.x == kIssuer) {
         issue();
         tc::mma_commit(&sm.mma_bar);
     }
+}
+
+__device__ __forceinline__ void mma_wait(Smem& sm, uint32_t& mph) {
     if (!tc::mbar_wait(&sm.mma_bar, mph, 1u << 26)) atomicExch(&sm.mma_err, 1);
     mph ^= 1u;
     tc::fence_after();
@@ -838,7 +876,8 @@ __device__ __forceinline__ void mma_round(Smem& sm, uint32_t& mph, IssueF issue)
 // stage rows 0..36 of Z^T for candidates [c0, c0+n): z' (feature rows 0..35, zero beyond
 // nz) and the constant one (row 36)
 template <bool BF16, bool INTFRAC>
-__device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, int nz, float shift) {
+__device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, int nz, float shift, uint16_t* t0,
+                                         uint16_t* t1, uint16_t* t2) {
     Hql& h = sm.hql;
     // live rows: the nz = 4 + Ny features and the constant (row 36); the other rows stay
     // at the zeros the pass started from.  Row slot ri < nz is feature ri, slot nz the
@@ -862,8 +901,8 @@ __device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, int nz, float 
             }
             v[t] = x;
         }
-        if (INTFRAC) store8_int_frac<BF16>(h.mx.t0, h.mx.t1, h.mx.t2, a, 8 * g8, 64, v);
-        else store8_split<BF16>(h.mx.t0, h.mx.t1, a, 8 * g8, 64, v);
+        if (INTFRAC) store8_int_frac<BF16>(t0, t1, t2, a, 8 * g8, 64, v);
+        else store8_split<BF16>(t0, t1, a, 8 * g8, 64, v);
     }
 }
 
@@ -871,75 +910,100 @@ __device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, int nz, float 
 // z' = n + f (integer part n, fraction f = fh + fl).  The integer products n_a n_b are
 // exact in 16 bits and their sum over 4 chunks (256 candidates, |n| <= 255: at most
 // 16,646,400) stays below 2^24, so the FP32 accumulator holds it exactly; it is read out
-// every 4 chunks into int32.  The
-// fractional cross terms n f + f n + f f accumulate in FP32 in a second accumulator
-// (tensor memory columns 64..111).  The same integer / fraction split as the CUDA-core
-// path, so the covariance keeps its precision through the cancellation in Eq. (8).
+// every 4 chunks into int32.  The fractional terms n f^T + f n^T + fh fh^T are symmetric
+// in pairs: X = n (fh + fl)^T (tensor memory columns 64..111) and Y = fh fh^T (columns
+// 128..175) accumulate in FP32, and the readout forms X + X^T + Y.  The same integer /
+// fraction split as the CUDA-core path, so the covariance keeps its precision through the
+// cancellation in Eq. (8).  Row 36 of the tiles is the constant one (n = 1, f = 0), so
+// column 36 of the integer sums holds sum_j n_a and (X + X^T)[a][36] holds sum_j f_a.
 template <bool BF16>
 __device__ __noinline__ void h1_mixed(int M, int nz, float shift, uint32_t tmem, uint32_t mph) {
     Smem& sm = smem_ref();
     Hql& h = sm.hql;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nchunks = (M + kCh - 1) / kCh;
-    const uint32_t idesc = tc::idesc_f16(128, 48, BF16);
+    const uint32_t idesc = tc::idesc_f16(64, 48, BF16);
     __syncthreads();  // the tiles share storage with buffers of the previous phase
-    zero_tiles(h);
+    // both buffers (rows past the live features stay zero) and the integer sums
+    zero_region(h, 0, 2 * tl::kH1Buf);
+    zero_region(h, tl::kH1Sums, tl::kH1SumsBytes);
     __syncthreads();
-    const int arow = 32 * wid + lane;  // warps 0, 1: the row of D this thread reads
-    // integer sums: the thread's own row of an int32 array in tile t3 (unused by this pass,
-    // cleared above; p1 shares storage with the live tiles t1, t2)
-    int(*nacc)[40] = reinterpret_cast<int(*)[40]>(h.mx.t3);
-    static_assert(sizeof(h.mx.t3) >= 36 * 40 * sizeof(int), "integer sums fit tile t3");
+    // warps 0..2, lanes 0..15: row arow of D (M = 64 layout), for arow <= 36
+    const int arow = 16 * wid + lane;
+    const bool reader = wid < 3 && lane < 16 && arow < 37;
+    const uint32_t tlane = (uint32_t)(32 * wid) << 16;
+    // integer sums: the thread's own row of an int32 array past the tiles (p1 shares
+    // storage with the tiles)
+    int(*nacc)[40] = reinterpret_cast<int(*)[40]>(tile(h, tl::kH1Sums));
+    auto tb = [&](int b, int t) { return tile(h, (uint32_t)b * tl::kH1Buf + (uint32_t)t * tl::kH1Tile); };
+    stage_zt<BF16, true>(sm, 0, min(kCh, M), nz, shift, tb(0, 0), tb(0, 1), tb(0, 2));
     for (int ch = 0; ch < nchunks; ++ch) {
-        const int c0 = ch * kCh, n = min(kCh, M - c0);
-        stage_zt<BF16, true>(sm, c0, n, nz, shift);
-        mma_round(sm, mph, [&]() {
+        const int b = ch & 1;
+        tiles_ready();
+        mma_issue(sm, [&]() {
             const uint32_t sbo = (64 / 8) * 128;
-            const uint32_t an = tc::smem_addr(h.mx.t0), ah = tc::smem_addr(h.mx.t1),
-                           al = tc::smem_addr(h.mx.t2);
+            const uint32_t an = tc::smem_addr(tb(b, 0)), ah = tc::smem_addr(tb(b, 1)),
+                           al = tc::smem_addr(tb(b, 2));
             for (int kk = 0; kk < 4; ++kk) {
                 const uint32_t o = (uint32_t)kk * 256u;
                 const uint64_t dn = tc::smem_desc(an + o, 128, sbo), dh = tc::smem_desc(ah + o, 128, sbo),
                                dl = tc::smem_desc(al + o, 128, sbo);
                 tc::mma_f16(tmem, dn, dn, idesc, (ch & 3) != 0 || kk > 0);  // integer part: 4 chunks
-                tc::mma_f16(tmem + 64, dn, dh, idesc, ch > 0 || kk > 0);
-                tc::mma_f16(tmem + 64, dh, dn, idesc, true);
+                tc::mma_f16(tmem + 64, dn, dh, idesc, ch > 0 || kk > 0);    // X = n (fh + fl)^T
                 tc::mma_f16(tmem + 64, dn, dl, idesc, true);
-                tc::mma_f16(tmem + 64, dl, dn, idesc, true);
-                tc::mma_f16(tmem + 64, dh, dh, idesc, true);
+                tc::mma_f16(tmem + 128, dh, dh, idesc, ch > 0 || kk > 0);   // Y = fh fh^T
             }
         });
-        if (wid < 2 && ((ch & 3) == 3 || ch == nchunks - 1)) {  // exact sums into int32
+        if (ch + 1 < nchunks) {  // the next chunk, while these MMAs run
+            const int c1 = (ch + 1) * kCh;
+            stage_zt<BF16, true>(sm, c1, min(kCh, M - c1), nz, shift, tb(b ^ 1, 0), tb(b ^ 1, 1), tb(b ^ 1, 2));
+        }
+        mma_wait(sm, mph);
+        if (wid < 3 && ((ch & 3) == 3 || ch == nchunks - 1)) {  // exact sums into int32
             for (int c = 0; c < 5; ++c) {  // columns 0..39 in groups of 8 (36: column sums)
                 float D[8];
-                tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 8 * c, D);
-                if (arow < 36) {
+                tc::tmem_ld8(tmem + tlane + 8 * c, D);
+                if (reader && arow < 36) {
 #pragma unroll
                     for (int t = 0; t < 8; ++t) nacc[arow][8 * c + t] += __float2int_rn(D[t]);
                 }
             }
         }
-        // (the next chunk's mma_round orders these tensor-memory reads before its MMAs)
+        // (the next chunk's tiles_ready orders these tensor-memory reads before its MMAs)
     }
-    // every MMA has completed: the operand tiles are dead and p1 may take the sums
-    if (wid < 2) {
+    // every MMA has completed: the operand tiles are dead.  X goes to a scratch array at
+    // the start of the region (p1 and the integer sums lie past it), X + Y to the row of
+    // cfrac; then cfrac += X^T.
+    float(*xs)[40] = reinterpret_cast<float(*)[40]>(tile(h, 0));
+    static_assert(37 * 40 * sizeof(float) <= 2 * tl::kH1Buf, "X scratch inside the tiles");
+    if (wid < 3) {
         for (int c = 0; c < 5; ++c) {
-            float F[8];
-            tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 64 + 8 * c, F);
-            if (arow < 36) {
+            float X[8], Y[8];
+            tc::tmem_ld8(tmem + tlane + 64 + 8 * c, X);
+            tc::tmem_ld8(tmem + tlane + 128 + 8 * c, Y);
+            if (reader) {
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                     const int b = 8 * c + t;
-                    if (b < 36) {
-                        h.p1.cfrac[arow][b] = F[t];
-                        h.p1.cint[arow][b] = nacc[arow][b];
-                    } else if (b == 36) {
-                        h.colF[arow] = F[t];
-                        h.colNi[arow] = nacc[arow][36];
+                    xs[arow][b] = X[t];
+                    if (arow < 36 && b < 37) {
+                        if (b < 36) {
+                            h.p1.cfrac[arow][b] = X[t] + Y[t];
+                            h.p1.cint[arow][b] = nacc[arow][b];
+                        } else {
+                            h.colF[arow] = X[t] + Y[t];
+                            h.colNi[arow] = nacc[arow][36];
+                        }
                     }
                 }
             }
         }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 36 * 37; idx += kThreads) {
+        const int a = idx / 37, b = idx - a * 37;
+        if (b < 36) h.p1.cfrac[a][b] += xs[b][a];
+        else h.colF[a] += xs[36][a];
     }
     tc::fence_before();
     __syncthreads();
@@ -953,22 +1017,25 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nchunks = (M + kCh - 1) / kCh;
     __syncthreads();  // the tiles share storage with buffers of the previous phase
-    zero_tiles(h);
-    __syncthreads();
-    // B = L^-1 (32 rows k x 32 columns l), staged once into t2/t3
+    // B = L^-1 (32 rows k x 32 columns l), staged once
+    uint16_t* bhi = tile(h, tl::kH2B);
+    uint16_t* blo = tile(h, tl::kH2B + tl::kH2BTile);
     if (tid < 128) {
         const int k = (tid & 7) | ((tid >> 5) << 3), l8 = (tid >> 3) & 3;  // conflict-free stores
         float v[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) v[t] = h.Linv[k][8 * l8 + t];
-        store8_split<BF16>(h.mx.t2, h.mx.t3, k, 8 * l8, 32, v);
+        store8_split<BF16>(bhi, blo, k, 8 * l8, 32, v);
     }
-    float lmin = INFINITY;
-    for (int ch = 0; ch < nchunks; ++ch) {
+    // A = E (rows: candidates, columns: context) of chunk ch into buffer ch & 1, one task per
+    // thread (every row and column of the tile); a quarter-warp stores 8 consecutive rows of
+    // one column group (conflict-free)
+    auto stage_a = [&](int ch) {
         const int c0 = ch * kCh, n = min(kCh, M - c0);
-        {  // A = E (rows: candidates, columns: context), one task per thread; a quarter-warp
-           // stores 8 consecutive rows of one column group (conflict-free)
-            const int j = (tid & 7) | ((tid >> 5) << 3), l8 = (tid >> 3) & 3;
+        const uint32_t o = (uint32_t)(ch & 1) * tl::kH2ABuf;
+        {  // 64 rows x 4 column groups: one task per thread
+            const int q = tid;
+            const int j = (q & 7) | ((q >> 5) << 3), l8 = (q >> 3) & 3;
             float v[8];
             const int base = j < n ? h.cand[c0 + j] : 0;
 #pragma unroll
@@ -976,26 +1043,43 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
                 const int l = 8 * l8 + t;
                 v[t] = (j < n && l < ny) ? (sm.S[base + h.off[l]] - shift) - h.ys[l] : 0.0f;
             }
-            store8_split<BF16>(h.mx.t0, h.mx.t1, j, 8 * l8, 32, v);
+            store8_split<BF16>(tile(h, o), tile(h, o + tl::kH2A), j, 8 * l8, 32, v);
         }
-        mma_round(sm, mph, [&]() { mma3(tmem, h.mx.t0, h.mx.t1, h.mx.t2, h.mx.t3, 32, tc::idesc_f16(128, 32, BF16), false); });
-        if (wid < 2) {
-            const int j = 32 * wid + lane;
+    };
+    // d_j = ||u_j||^2 of chunk ch from tensor-memory columns 32 (ch & 1) .. +31; candidate
+    // j of the chunk in lane 16w + j%16 of warp w = j / 16 (M = 64 layout)
+    float lmin = INFINITY;
+    auto read_d = [&](int ch) {
+        if (wid < 4) {
+            const int c0 = ch * kCh, n = min(kCh, M - c0), j = 16 * wid + lane;
             float dd = 0.0f;
             for (int c = 0; c < 4; ++c) {  // groups of 8 columns (few live registers)
                 float u[8];
-                tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 8 * c, u);
+                tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 32 * (ch & 1) + 8 * c, u);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) dd = __fmaf_rn(u[k], u[k], dd);
             }
-            if (j < n) {
+            if (lane < 16 && j < n) {
                 h.d[c0 + j] = dd;
                 lmin = fminf(lmin, dd);
             }
         }
-        tc::fence_before();
-        __syncthreads();  // tensor memory read before the next chunk's MMAs
+    };
+    stage_a(0);
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const uint32_t o = (uint32_t)(ch & 1) * tl::kH2ABuf;
+        tiles_ready();
+        mma_issue(sm, [&]() {
+            mma3(tmem + 32 * (ch & 1), tile(h, o), tile(h, o + tl::kH2A), bhi, blo, 32,
+                 tc::idesc_f16(64, 32, BF16), false);
+        });
+        if (ch + 1 < nchunks) stage_a(ch + 1);  // while the MMAs of chunk ch run
+        if (ch > 0) read_d(ch - 1);            // (the other tensor-memory columns)
+        mma_wait(sm, mph);
     }
+    read_d(nchunks - 1);
+    tc::fence_before();
+    __syncthreads();  // tensor memory read before the next pass's MMAs
     return lmin;
 }
 
@@ -1009,14 +1093,18 @@ __device__ __noinline__ void h3_mixed(const KParams& P, int M, int nz, float shi
     const int nchunks = (M + kCh - 1) / kCh;
     const int nb = P.nbeta;
     __syncthreads();  // the tiles share storage with buffers of the previous phase
-    zero_tiles(h);
+    zero_region(h, tl::kH3Z, 2 * tl::kH3ZBuf);  // Z' rows past the live features stay zero
     __syncthreads();
-    for (int ch = 0; ch < nchunks; ++ch) {
-        const int c0 = ch * kCh, n = min(kCh, M - c0);
-        stage_zt<BF16, false>(sm, c0, n, nz, shift);
-        {  // A = W (rows: beta, columns: candidates), one task per thread; a quarter-warp
-           // stores 8 consecutive rows of one column group (conflict-free)
-            const int b = (tid & 7) | ((tid >> 6) << 3), g8 = (tid >> 3) & 7;
+    auto zt = [&](int b, int t) { return tile(h, tl::kH3Z + (uint32_t)b * tl::kH3ZBuf + (uint32_t)t * tl::kH3ZTile); };
+    auto wt = [&](int b, int t) { return tile(h, (uint32_t)b * tl::kH3WBuf + (uint32_t)t * tl::kH3W); };
+    auto stage = [&](int ch) {
+        const int c0 = ch * kCh, n = min(kCh, M - c0), bf = ch & 1;
+        stage_zt<BF16, false>(sm, c0, n, nz, shift, zt(bf, 0), zt(bf, 1), nullptr);
+        // A = W (rows: beta, columns: candidates), 32 rows x 8 column groups; a quarter-warp
+        // stores 8 consecutive rows of one column group (conflict-free)
+        {  // one task per thread
+            const int q = tid;
+            const int b = (q & 7) | ((q >> 6) << 3), g8 = (q >> 3) & 7;
             if (b < nb) {
                 float v[8];
                 const float ib = P.inv2beta[b];
@@ -1025,19 +1113,29 @@ __device__ __noinline__ void h3_mixed(const KParams& P, int M, int nz, float shi
                     const int j = 8 * g8 + t;
                     v[t] = j < n ? __expf(-(h.d[c0 + j] - dmin) * ib) : 0.0f;
                 }
-                store8_split<BF16>(h.mx.t2, h.mx.t3, b, 8 * g8, 64, v);
+                store8_split<BF16>(wt(bf, 0), wt(bf, 1), b, 8 * g8, 64, v);
             }
         }
-        mma_round(sm, mph, [&]() { mma3(tmem, h.mx.t2, h.mx.t3, h.mx.t0, h.mx.t1, 64, tc::idesc_f16(128, 48, BF16), ch > 0); });
+    };
+    stage(0);
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const int bf = ch & 1;
+        tiles_ready();
+        mma_issue(sm, [&]() {
+            mma3(tmem, wt(bf, 0), wt(bf, 1), zt(bf, 0), zt(bf, 1), 64, tc::idesc_f16(64, 48, BF16), ch > 0);
+        });
+        if (ch + 1 < nchunks) stage(ch + 1);  // while the MMAs of chunk ch run
+        mma_wait(sm, mph);
     }
-    if (wid == 0) {
+    if (wid < 2) {  // beta b in lane 16w + b%16 of warp w = b / 16 (M = 64 layout)
+        const int b = 16 * wid + lane;
         for (int c = 0; c < 5; ++c) {  // columns 0..39 in groups of 8
             float D[8];
-            tc::tmem_ld8(tmem + 8 * c, D);
-            if (lane < nb) {
+            tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 8 * c, D);
+            if (lane < 16 && b < nb) {
 #pragma unroll
                 for (int t = 0; t < 8; ++t)
-                    if (8 * c + t < 37) h.accBd[lane][8 * c + t] = df_make(D[t]);
+                    if (8 * c + t < 37) h.accBd[b][8 * c + t] = df_make(D[t]);
             }
         }
     }
@@ -1877,9 +1975,10 @@ __device__ __noinline__ void release_dependants(const WorkDev& W, const FrameDev
     }
 }
 
-// tensor-memory columns per CTA: H1 uses 0..111
+// tensor-memory columns per CTA: H1 uses 0..47, 64..111 and 128..175 (two CTAs per SM
+// take the SM's 512 columns)
 template <int MIXED>
-constexpr uint32_t kTmemCols = 128u;
+constexpr uint32_t kTmemCols = 256u;
 
 template <int MIXED>
 __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_constant__ WorkDev W,

@@ -734,32 +734,82 @@ __device__ __forceinline__ void whiten_tile(const Hql& h, int buf, int ny, int t
 // two 16-bit parts, v ~ hi + lo (BF16: ~16 significant bits; FP16: ~22), and every product
 // is accumulated as hi*hi + hi*lo + lo*hi in FP32 tensor memory.
 
+// The splits stay off the format-conversion unit, which runs at a fraction of the FP32 rate
+// and set the staging time of the passes:
+//   BF16: round-to-nearest-even on the FP32 bits with integer operations (exact);
+//   FP16: the high part is v rounded to 11 significant bits by Veltkamp's splitting in FP32
+//         (non-contracting intrinsics), the low part v - hi exactly, and each pair of values
+//         is converted by one packed conversion.
+__device__ __forceinline__ uint32_t bf16_bits_rn(float v) {  // finite v
+    const uint32_t u = __float_as_uint(v);
+    return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+
+__device__ __forceinline__ float veltkamp_hi11(float v) {  // v to 11 significant bits
+    const float g = __fmul_rn(8193.0f, v);  // 2^13 + 1
+    return __fadd_rn(g, __fsub_rn(v, g));
+}
+
+__device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {  // a low, b high, RN
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// the pair (v0, v1) as packed high halves and packed low halves
 template <bool BF16>
-__device__ __forceinline__ void split16(float v, uint16_t& hi, uint16_t& lo) {
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi2, uint32_t& lo2) {
     if (BF16) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        hi = __bfloat16_as_ushort(h);
-        lo = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+        const uint32_t h0 = bf16_bits_rn(v0), h1 = bf16_bits_rn(v1);
+        const uint32_t l0 = bf16_bits_rn(__fsub_rn(v0, __uint_as_float(h0 << 16)));
+        const uint32_t l1 = bf16_bits_rn(__fsub_rn(v1, __uint_as_float(h1 << 16)));
+        hi2 = h0 | (h1 << 16);
+        lo2 = l0 | (l1 << 16);
     } else {
-        const __half h = __float2half_rn(v);
-        hi = __half_as_ushort(h);
-        lo = __half_as_ushort(__float2half_rn(v - __half2float(h)));
+        const float h0 = veltkamp_hi11(v0), h1 = veltkamp_hi11(v1);
+        hi2 = pack_f16x2(h0, h1);
+        lo2 = pack_f16x2(__fsub_rn(v0, h0), __fsub_rn(v1, h1));
     }
 }
 
-// 8 consecutive K elements of row r of a K-major tile with K columns: one 16-byte row of a
-// core matrix in each of the hi and lo tiles
+// an integer-valued pair (|n| <= 256: exact in both formats), packed
 template <bool BF16>
+__device__ __forceinline__ uint32_t pack_int2(float n0, float n1) {
+    if (BF16) return (__float_as_uint(n0) >> 16) | (__float_as_uint(n1) & 0xFFFF0000u);
+    return pack_f16x2(n0, n1);
+}
+
+// the same pair split through the format-conversion unit (round to nearest even twice)
+template <bool BF16>
+__device__ __forceinline__ void split2_cvt(float v0, float v1, uint32_t& hi2, uint32_t& lo2) {
+    uint16_t h[2], l[2];
+    const float v[2] = {v0, v1};
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        if (BF16) {
+            const __nv_bfloat16 x = __float2bfloat16_rn(v[t]);
+            h[t] = __bfloat16_as_ushort(x);
+            l[t] = __bfloat16_as_ushort(__float2bfloat16_rn(v[t] - __bfloat162float(x)));
+        } else {
+            const __half x = __float2half_rn(v[t]);
+            h[t] = __half_as_ushort(x);
+            l[t] = __half_as_ushort(__float2half_rn(v[t] - __half2float(x)));
+        }
+    }
+    hi2 = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+    lo2 = (uint32_t)l[0] | ((uint32_t)l[1] << 16);
+}
+
+// 8 consecutive K elements of row r of a K-major tile with K columns: one 16-byte row of a
+// core matrix in each of the hi and lo tiles.  CVT: split through the conversion unit (the
+// whitening pass, H2, measured faster that way; the other passes measured faster without).
+template <bool BF16, bool CVT = false>
 __device__ __forceinline__ void store8_split(uint16_t* thi, uint16_t* tlo, int r, int k0, int K,
                                              const float v[8]) {
     uint32_t h[4], l[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        uint16_t h0, l0, h1, l1;
-        split16<BF16>(v[2 * q], h0, l0);
-        split16<BF16>(v[2 * q + 1], h1, l1);
-        h[q] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-        l[q] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+        if (CVT) split2_cvt<BF16>(v[2 * q], v[2 * q + 1], h[q], l[q]);
+        else split2<BF16>(v[2 * q], v[2 * q + 1], h[q], l[q]);
     }
     const uint32_t off = tc::kmajor_offset(r, k0, K) >> 1;  // in 16-bit elements
     *reinterpret_cast<uint4*>(thi + off) = make_uint4(h[0], h[1], h[2], h[3]);
@@ -772,20 +822,13 @@ template <bool BF16>
 __device__ __forceinline__ void store8_int_frac(uint16_t* tn, uint16_t* tfh, uint16_t* tfl, int r,
                                                 int k0, int K, const float v[8]) {
     uint32_t n[4], fh[4], fl[4];
+    constexpr float kRnd = 12582912.0f;  // 1.5 * 2^23: x + kRnd - kRnd rounds to an integer (RN)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        uint16_t a[2], b[2], c[2];
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const float x = v[2 * q + t];
-            const float xn = rintf(x);
-            uint16_t dummy;
-            split16<BF16>(xn, a[t], dummy);
-            split16<BF16>(x - xn, b[t], c[t]);
-        }
-        n[q] = (uint32_t)a[0] | ((uint32_t)a[1] << 16);
-        fh[q] = (uint32_t)b[0] | ((uint32_t)b[1] << 16);
-        fl[q] = (uint32_t)c[0] | ((uint32_t)c[1] << 16);
+        const float x0 = v[2 * q], x1 = v[2 * q + 1];
+        const float n0 = __fsub_rn(__fadd_rn(x0, kRnd), kRnd), n1 = __fsub_rn(__fadd_rn(x1, kRnd), kRnd);
+        n[q] = pack_int2<BF16>(n0, n1);
+        split2<BF16>(__fsub_rn(x0, n0), __fsub_rn(x1, n1), fh[q], fl[q]);
     }
     const uint32_t off = tc::kmajor_offset(r, k0, K) >> 1;
     *reinterpret_cast<uint4*>(tn + off) = make_uint4(n[0], n[1], n[2], n[3]);
@@ -1025,7 +1068,7 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
         float v[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) v[t] = h.Linv[k][8 * l8 + t];
-        store8_split<BF16>(bhi, blo, k, 8 * l8, 32, v);
+        store8_split<BF16, true>(bhi, blo, k, 8 * l8, 32, v);
     }
     // A = E (rows: candidates, columns: context) of chunk ch into buffer ch & 1, one task per
     // thread (every row and column of the tile); a quarter-warp stores 8 consecutive rows of
@@ -1043,7 +1086,7 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
                 const int l = 8 * l8 + t;
                 v[t] = (j < n && l < ny) ? (sm.S[base + h.off[l]] - shift) - h.ys[l] : 0.0f;
             }
-            store8_split<BF16>(tile(h, o), tile(h, o + tl::kH2A), j, 8 * l8, 32, v);
+            store8_split<BF16, true>(tile(h, o), tile(h, o + tl::kH2A), j, 8 * l8, 32, v);
         }
     };
     // d_j = ||u_j||^2 of chunk ch from tensor-memory columns 32 (ch & 1) .. +31; candidate

@@ -152,12 +152,17 @@ struct __align__(16) HqlP1 {                 // covariance / factorisation phase
     df32 X[32][33];
 };
 constexpr int kI0Pad = 36;   // leave-one-out members padded to whole 3-member tiles
-constexpr int kVs = 44;      // row stride of a whitened chunk (conflict-free 16-byte reads)
+// The leave-one-out pass works on candidate pairs (p, p + 32) of a chunk, interleaved in
+// shared memory so that 64-bit halves of a 16-byte load are the pair's values and the packed
+// two-lane FP32 instructions (f32x2) take them as they are.
+constexpr int kVp = 84;      // row stride of a whitened chunk pair: 40 columns x 2 (+4: 16-byte
+                             // reads of consecutive rows fall on distinct bank groups)
+constexpr int kWp = 76;      // row stride of the leave-one-out weights of a pair: 36 members x 2
 struct __align__(16) HqlP2 {                 // beta / leave-one-out phase
     union {
         struct {  // two buffers: chunk c is whitened while chunk c-1 is summed
-            __align__(16) float Vs[2][kCh][kVs];      // whitened chunk: x'(4) u(32) 1 pad
-            __align__(16) float Wt[2][kCh][kI0Pad];   // leave-one-out weights, candidate-major
+            __align__(16) float Vp[2][kCh / 2][kVp];  // whitened chunk: x'(4) u(32) 1 pad, pairs
+            __align__(16) float Wp[2][kCh / 2][kWp];  // leave-one-out weights per member, pairs
         };
         float mrg[kThreads][37];             // per-thread partial sums before a merge
         float accP[4][kI0Pad][40];           // leave-one-out sums of the candidate groups
@@ -1186,41 +1191,86 @@ __device__ __noinline__ void h3_mixed(const KParams& P, int M, int nz, float shi
     __syncthreads();
 }
 
+// packed two-lane FP32 (sm_100+): each lane an IEEE round-to-nearest operation
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2_pack(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 // Leave-one-out scores of one chunk (H5): thread (it, jq) owns members 3it..3it+2 against
 // candidates jq + L r (r < 64 / L), with L lanes per member triple (L = 16 or 32: fewer
 // candidates per thread when n0 is small).  Squared whitened distances, the chunk maximum
-// per member (shuffles over the L lanes), the new running maximum and the weights.
+// per member (shuffles over the L lanes), the new running maximum and the weights.  The
+// candidates jq + L q and jq + L q + 32 (q < R / 2) form pair q: their distances accumulate
+// in the two lanes of packed f32x2 operations, each lane in the order of the scalar form.
 template <int L>
 __device__ __forceinline__ void h5_scores(Hql& h, int vb_, int n0, int nyq, int n, int c0, float ib) {
-    constexpr int R = 64 / L;
+    constexpr int R = 64 / L, NP = R / 2;
     const int tid = threadIdx.x;
     const int it = tid / L, jq = tid % L;
     if (3 * it >= n0) return;  // (whole lane groups: L divides 32 or equals it)
     int selfc[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) selfc[a] = 3 * it + a < n0 ? h.i0[3 * it + a] : -2;
-    float d[3][R];
+    f32x2 d2[3][NP];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int r = 0; r < R; ++r) d[a][r] = 0.0f;
+        for (int q = 0; q < NP; ++q) d2[a][q] = 0ull;
     for (int l4 = 0; l4 < nyq; ++l4) {
-        float4 ua[3], vb[R];
+        float4 ua[3];
+        f32x2 vp[NP][4];  // pair q, component c (4 l4 + c of u): {candidate p, candidate p + 32}
 #pragma unroll
         for (int a = 0; a < 3; ++a) ua[a] = *reinterpret_cast<const float4*>(&h.UI[3 * it + a][4 * l4]);
 #pragma unroll
-        for (int r = 0; r < R; ++r) vb[r] = *reinterpret_cast<const float4*>(&h.p2.Vs[vb_][jq + L * r][4 + 4 * l4]);
+        for (int q = 0; q < NP; ++q) {
+            const float* row = &h.p2.Vp[vb_][jq + L * q][2 * (4 + 4 * l4)];
+            const ulonglong2 v01 = *reinterpret_cast<const ulonglong2*>(row);
+            const ulonglong2 v23 = *reinterpret_cast<const ulonglong2*>(row + 4);
+            vp[q][0] = v01.x;
+            vp[q][1] = v01.y;
+            vp[q][2] = v23.x;
+            vp[q][3] = v23.y;
+        }
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
+        for (int a = 0; a < 3; ++a) {
+            const float uc[4] = {ua[a].x, ua[a].y, ua[a].z, ua[a].w};
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float t;
-                t = ua[a].x - vb[r].x; d[a][r] = __fmaf_rn(t, t, d[a][r]);
-                t = ua[a].y - vb[r].y; d[a][r] = __fmaf_rn(t, t, d[a][r]);
-                t = ua[a].z - vb[r].z; d[a][r] = __fmaf_rn(t, t, d[a][r]);
-                t = ua[a].w - vb[r].w; d[a][r] = __fmaf_rn(t, t, d[a][r]);
+            for (int c = 0; c < 4; ++c) {
+                const f32x2 u2 = f2_pack(uc[c], uc[c]);
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    const f32x2 t = f2_sub(u2, vp[q][c]);
+                    d2[a][q] = f2_fma(t, t, d2[a][q]);
+                }
             }
+        }
     }
+    float d[3][R];  // candidate jq + L r: pair r mod NP... r = q (lane 0) or q + NP (lane 1)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int q = 0; q < NP; ++q) f2_unpack(d2[a][q], d[a][q], d[a][q + NP]);
     // the three members side by side: independent shuffle and exp chains
     float sc[3][R], mx[3], mold[3];
 #pragma unroll
@@ -1246,8 +1296,10 @@ __device__ __forceinline__ void h5_scores(Hql& h, int vb_, int n0, int nyq, int 
         const int i = 3 * it + a;
         const float mnew = fmaxf(mold[a], mx[a]);
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-            h.p2.Wt[vb_][jq + L * r][i] = sc[a][r] == -INFINITY ? 0.0f : __expf(sc[a][r] - mnew);
+        for (int r = 0; r < R; ++r) {
+            const int j = jq + L * r;  // pair j & 31, lane j >> 5
+            h.p2.Wp[vb_][j & 31][2 * i + (j >> 5)] = sc[a][r] == -INFINITY ? 0.0f : __expf(sc[a][r] - mnew);
+        }
         if (jq == 0) {
             h.p2.scl[vb_][i] = mold[a] == -INFINITY ? 0.0f : __expf(mold[a] - mnew);
             h.p2.mrow[i] = mnew;
@@ -1772,11 +1824,11 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
         const int jg = tid / tasks, rr = tid - jg * tasks, ib4 = rr / nkq, kq = rr - ib4 * nkq;
         const int kb = kq < kql ? kq : 9;
         const bool ac_act = jg < G;
-        float acc[4][4];
+        f32x2 acc2[4][4];  // lanes: candidate pairs' first and second halves
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[a][q] = 0.0f;
+            for (int q = 0; q < 4; ++q) acc2[a][q] = 0ull;
         if (tid < kI0Pad) {
             h.p2.mrow[tid] = -INFINITY;
             if (tid >= n0)
@@ -1793,18 +1845,24 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
                 const float4 s4 = *reinterpret_cast<const float4*>(&h.p2.scl[pb][4 * ib4]);
                 const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < 4; ++a) {
+                    const f32x2 s2 = f2_pack(sv[a], sv[a]);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[a][q] *= sv[a];
-                for (int j = jg; j < pn; j += G) {
-                    const float4 w4 = *reinterpret_cast<const float4*>(&h.p2.Wt[pb][j][4 * ib4]);
-                    const float4 v4 = *reinterpret_cast<const float4*>(&h.p2.Vs[pb][j][4 * kb]);
-                    const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
-                    const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+                    for (int q = 0; q < 4; ++q) acc2[a][q] = f2_mul(acc2[a][q], s2);
+                }
+                // candidate pairs (p, p + 32); past pn the weights are zero
+                const int npair = min(kCh / 2, pn);
+                for (int p = jg; p < npair; p += G) {
+                    const ulonglong2 w01 = *reinterpret_cast<const ulonglong2*>(&h.p2.Wp[pb][p][8 * ib4]);
+                    const ulonglong2 w23 = *reinterpret_cast<const ulonglong2*>(&h.p2.Wp[pb][p][8 * ib4 + 4]);
+                    const ulonglong2 v01 = *reinterpret_cast<const ulonglong2*>(&h.p2.Vp[pb][p][8 * kb]);
+                    const ulonglong2 v23 = *reinterpret_cast<const ulonglong2*>(&h.p2.Vp[pb][p][8 * kb + 4]);
+                    const f32x2 wv[4] = {w01.x, w01.y, w23.x, w23.y};
+                    const f32x2 vv[4] = {v01.x, v01.y, v23.x, v23.y};
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[a][q] = __fmaf_rn(wv[a], vv[q], acc[a][q]);
+                        for (int q = 0; q < 4; ++q) acc2[a][q] = f2_fma(wv[a], vv[q], acc2[a][q]);
                 }
             }
             if (ch == nchunks) break;
@@ -1812,13 +1870,19 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
                 const int qw = wid & 3, jw = lane + 32 * (wid >> 2);
                 float ua[4], ub[4];
                 whiten_quads(h, buf, ny, jw, qw, ua, ub);
-                float* vrow = &h.p2.Vs[buf][jw][0];
-                *reinterpret_cast<float4*>(vrow + 4 + 4 * qw) = make_float4(ua[0], ua[1], ua[2], ua[3]);
-                *reinterpret_cast<float4*>(vrow + 4 + 4 * (7 - qw)) = make_float4(ub[0], ub[1], ub[2], ub[3]);
+                float* vrow = &h.p2.Vp[buf][lane][wid >> 2];  // column k at vrow[2 k]
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    vrow[2 * (4 + 4 * qw + r)] = ua[r];
+                    vrow[2 * (4 + 4 * (7 - qw) + r)] = ub[r];
+                }
                 if (qw == 0) {
-                    *reinterpret_cast<float4*>(vrow) = *reinterpret_cast<const float4*>(&h.Z[buf][jw][0]);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) vrow[2 * r] = h.Z[buf][jw][r];
                 } else if (qw == 1) {
-                    *reinterpret_cast<float4*>(vrow + 36) = make_float4(h.Z[buf][jw][36], 0.0f, 0.0f, 0.0f);
+                    vrow[2 * 36] = h.Z[buf][jw][36];
+#pragma unroll
+                    for (int r = 37; r < 40; ++r) vrow[2 * r] = 0.0f;
                 }
             }
             __syncthreads();
@@ -1830,12 +1894,20 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
             else h5_scores<16>(h, buf, n0, nyq, n, c0, ib);
             SK_PHASE(PH_X2);
         }
-        __syncthreads();  // Vs / Wt no longer needed: their storage takes the partial sums
+        __syncthreads();  // Vp / Wp no longer needed: their storage takes the partial sums
         if (ac_act) {
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 4; ++a) {
+                float acc[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float lo, hi;
+                    f2_unpack(acc2[a][q], lo, hi);
+                    acc[q] = lo + hi;
+                }
                 *reinterpret_cast<float4*>(&h.p2.accP[jg][4 * ib4 + a][4 * kb]) =
-                    make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+                    make_float4(acc[0], acc[1], acc[2], acc[3]);
+            }
         }
         __syncthreads();
         for (int idx = tid; idx < n0 * 37; idx += kThreads) {

@@ -1508,7 +1508,7 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
         }
         for (int k = 0; k < ny; ++k) {
             const df32 akk = h.p1.A[k][k];
-            const df32 rinv = df_div(df_make(1.0f), akk);
+            const df32 rinv = df_rcp(akk);
 #pragma unroll
             for (int q = 0; q < kPer; ++q) {
                 const int i = pi[q], j = pj[q];
@@ -1524,12 +1524,15 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
             }
             __syncthreads();
         }
-        // L^-1 = D^-1/2 X: kept in double-float in X, rounded to FP32 in Linv
+        // L^-1 = D^-1/2 X: kept in double-float in X, rounded to FP32 in Linv.  The row scales
+        // D^-1/2 once per row (in ebard, free until the beta pass).
+        if (tid < 32) h.ebard[tid] = tid < ny ? df_rcp(df_sqrt(h.p1.A[tid][tid])) : df_make(0.0f);
+        __syncthreads();
         for (int idx = tid; idx < 32 * 32; idx += kThreads) {
             const int i = idx >> 5, j = idx & 31;
             float v = 0.0f;
             if (i < ny && j <= i) {
-                const df32 rs = df_div(df_make(1.0f), df_sqrt(h.p1.A[i][i]));
+                const df32 rs = h.ebard[i];
                 const df32 l = (j == i) ? rs : df_mul(h.p1.X[i][j], rs);
                 v = df_to_f(l);
                 h.p1.X[i][j] = l;
@@ -1540,23 +1543,40 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
     __syncthreads();
     // G = C_XY L^-T (4 x ny): G[a][i] = sum_k C_XY[a][k] Linv[i][k], in double-float;
     // kept in FP32 for the leave-one-out corrections and in double-float (in the first
-    // rows of A, no longer needed) for K
-    if (tid < 128) {
-        const int a = tid >> 5, i = tid & 31;
+    // rows of A, no longer needed) for K.  Thread (a, i, half): the sums over k < 16 and
+    // k >= 16 in adjacent lanes, added as (lower half) + (upper half) in both.
+    {
+        const int half = tid & 1, i = (tid >> 1) & 31, a = tid >> 6;
         df32 g = df_make(0.0f);
-        if (i < ny)
-            for (int k = 0; k <= i; ++k) g = df_add(g, df_mul(h.cxy[a][k], h.p1.X[i][k]));
-        h.G[a][i] = df_to_f(g);
-        h.p1.A[a][i] = g;
+        if (i < ny) {
+            const int k1 = min(i, half ? 31 : 15);
+            for (int k = half ? 16 : 0; k <= k1; ++k) g = df_add(g, df_mul(h.cxy[a][k], h.p1.X[i][k]));
+        }
+        df32 o;
+        o.hi = __shfl_xor_sync(0xffffffffu, g.hi, 1);
+        o.lo = __shfl_xor_sync(0xffffffffu, g.lo, 1);
+        g = half ? df_add(o, g) : df_add(g, o);
+        __syncthreads();  // every read of A (and of X) for G done before A's rows take G
+        if (half == 0) {
+            h.G[a][i] = df_to_f(g);
+            h.p1.A[a][i] = g;
+        }
     }
     __syncthreads();
-    // K = C_XY C_YY^-1 = G L^-1: K[a][j] = sum_{i >= j} G[a][i] Linv[i][j] (double-float)
-    if (tid < 128) {
-        const int a = tid >> 5, j = tid & 31;
+    // K = C_XY C_YY^-1 = G L^-1: K[a][j] = sum_{i >= j} G[a][i] Linv[i][j] (double-float),
+    // split over i < 16 and i >= 16 in the same way
+    {
+        const int half = tid & 1, j = (tid >> 1) & 31, a = tid >> 6;
         df32 kk = df_make(0.0f);
-        if (j < ny)
-            for (int i = j; i < ny; ++i) kk = df_add(kk, df_mul(h.p1.A[a][i], h.p1.X[i][j]));
-        h.K[a][j] = kk;
+        if (j < ny) {
+            const int i1 = half ? ny - 1 : min(15, ny - 1);
+            for (int i = max(j, half ? 16 : 0); i <= i1; ++i) kk = df_add(kk, df_mul(h.p1.A[a][i], h.p1.X[i][j]));
+        }
+        df32 o;
+        o.hi = __shfl_xor_sync(0xffffffffu, kk.hi, 1);
+        o.lo = __shfl_xor_sync(0xffffffffu, kk.lo, 1);
+        kk = half ? df_add(o, kk) : df_add(kk, o);
+        if (half == 0) h.K[a][j] = kk;
     }
     SK_PHASE(PH_CHOL);
 

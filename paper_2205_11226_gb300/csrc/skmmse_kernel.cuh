@@ -152,23 +152,9 @@ struct __align__(16) HqlP1 {                 // covariance / factorisation phase
     df32 X[32][33];
 };
 constexpr int kI0Pad = 36;   // leave-one-out members padded to whole 3-member tiles
-// The leave-one-out pass works on candidate pairs (p, p + 32) of a chunk, interleaved in
-// shared memory so that 64-bit halves of a 16-byte load are the pair's values and the packed
-// two-lane FP32 instructions (f32x2) take them as they are.
-constexpr int kVp = 84;      // row stride of a whitened chunk pair: 40 columns x 2 (+4: 16-byte
-                             // reads of consecutive rows fall on distinct bank groups)
-constexpr int kWp = 76;      // row stride of the leave-one-out weights of a pair: 36 members x 2
-struct __align__(16) HqlP2 {                 // beta / leave-one-out phase
-    union {
-        struct {  // two buffers: chunk c is whitened while chunk c-1 is summed
-            __align__(16) float Vp[2][kCh / 2][kVp];  // whitened chunk: x'(4) u(32) 1 pad, pairs
-            __align__(16) float Wp[2][kCh / 2][kWp];  // leave-one-out weights per member, pairs
-        };
-        float mrg[kThreads][37];             // per-thread partial sums before a merge
-        float accP[4][kI0Pad][40];           // leave-one-out sums of the candidate groups
-    };
-    float mrow[kI0Pad];                      // running maximum score per member
-    float scl[2][kI0Pad];                    // rescaling of the member's sums for a chunk
+constexpr int kWb = 44;      // leave-one-out candidate buffer row: x'(4) G u(4) pad(4) u(32)
+struct __align__(16) HqlP2 {                 // beta phase (CUDA-core form)
+    float mrg[kThreads][37];                 // per-thread partial sums before a merge
 };
 
 struct __align__(16) Hql {
@@ -178,6 +164,7 @@ struct __align__(16) Hql {
     float G[4][32];
     df32 cxy[4][32];            // C_XY (double-float)
     df32 K[4][32];              // C_XY C_YY^-1 (double-float)
+    __align__(16) float Kf[4][36];  // K rounded to FP32 (rows padded: conflict-free column reads)
     __align__(16) float ys[36];  // y0 - shift (compacted)
     short off[36];              // compacted context offsets rel. window top-left
     int i0[kMaxI0];             // I0 candidate indices, ascending
@@ -198,7 +185,7 @@ struct __align__(16) Hql {
     float alpha;
     __align__(16) float UI[kI0Pad][36];      // whitened I0 members, u_i = L^-1 (y_i - y0)
     float XI[kMaxI0][4];                     // x_i - shift of the I0 members
-    float accI[kMaxI0][37];                  // merged leave-one-out sums: x'(4) u(32) sum w
+    float accI[kMaxI0][12];                  // merged leave-one-out sums: x'(4) G u(4) sum w
     union {
         df32 accBd[kMaxBeta][kZs];  // beta-pass sums (double-float), end of H3 only
         struct {  // CUDA-core staging and phase buffers
@@ -209,6 +196,10 @@ struct __align__(16) Hql {
             };
         };
         __align__(16) uint16_t mx[32768];  // tensor-core operand tiles (64 KB; layout in tl::)
+        struct {  // leave-one-out pass: per-warp candidate buffers and the warps' partial sums
+            __align__(16) float Wb[kWarps][32][kWb];
+            float Mg[kWarps][33][10];
+        } h5;
     };
 };
 
@@ -670,43 +661,6 @@ __device__ __forceinline__ bool hql_stage_split(Smem& sm, int c0, int n, float s
 
 // whitened coordinates of candidates tj, tj+1 (rows of Z[buf]), coordinates 4tq..4tq+3:
 // u = L^-1 (y_j - y0)
-// whitened coordinates 4q..4q+3 (ua) and 4(7-q)..4(7-q)+3 (ub) of candidate j (row j of
-// Z[buf]).  L^-1 is lower triangular, so the two groups take q+1 and 8-q steps: 9 for every
-// q.  Callers give all lanes of a warp the same q (no divergence) and one candidate each.
-__device__ __forceinline__ void whiten_quads(const Hql& h, int buf, int ny, int j, int q,
-                                             float ua[4], float ub[4]) {
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        ua[r] = 0.0f;
-        ub[r] = 0.0f;
-    }
-    const int qb = 7 - q;
-    for (int l4 = 0; l4 <= qb; ++l4) {
-        if (4 * l4 >= ny) break;
-        const float4 ev = *reinterpret_cast<const float4*>(&h.Z[buf][j][4 + 4 * l4]);
-        const float4 ysv = *reinterpret_cast<const float4*>(&h.ys[4 * l4]);
-        const float e[4] = {ev.x - ysv.x, ev.y - ysv.y, ev.z - ysv.z, ev.w - ysv.w};
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float4 lv = *reinterpret_cast<const float4*>(&h.Linv[4 * qb + r][4 * l4]);
-            ub[r] = __fmaf_rn(lv.x, e[0], ub[r]);
-            ub[r] = __fmaf_rn(lv.y, e[1], ub[r]);
-            ub[r] = __fmaf_rn(lv.z, e[2], ub[r]);
-            ub[r] = __fmaf_rn(lv.w, e[3], ub[r]);
-        }
-        if (l4 <= q) {
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const float4 lv = *reinterpret_cast<const float4*>(&h.Linv[4 * q + r][4 * l4]);
-                ua[r] = __fmaf_rn(lv.x, e[0], ua[r]);
-                ua[r] = __fmaf_rn(lv.y, e[1], ua[r]);
-                ua[r] = __fmaf_rn(lv.z, e[2], ua[r]);
-                ua[r] = __fmaf_rn(lv.w, e[3], ua[r]);
-            }
-        }
-    }
-}
-
 __device__ __forceinline__ void whiten_tile(const Hql& h, int buf, int ny, int tj, int tq,
                                             float u0[4], float u1[4]) {
 #pragma unroll
@@ -1206,105 +1160,31 @@ __device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
-__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
-    f32x2 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
 __device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
     f32x2 r;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
     return r;
 }
 
-// Leave-one-out scores of one chunk (H5): thread (it, jq) owns members 3it..3it+2 against
-// candidates jq + L r (r < 64 / L), with L lanes per member triple (L = 16 or 32: fewer
-// candidates per thread when n0 is small).  Squared whitened distances, the chunk maximum
-// per member (shuffles over the L lanes), the new running maximum and the weights.  The
-// candidates jq + L q and jq + L q + 32 (q < R / 2) form pair q: their distances accumulate
-// in the two lanes of packed f32x2 operations, each lane in the order of the scalar form.
-template <int L>
-__device__ __forceinline__ void h5_scores(Hql& h, int vb_, int n0, int nyq, int n, int c0, float ib) {
-    constexpr int R = 64 / L, NP = R / 2;
-    const int tid = threadIdx.x;
-    const int it = tid / L, jq = tid % L;
-    if (3 * it >= n0) return;  // (whole lane groups: L divides 32 or equals it)
-    int selfc[3];
+// one step of a max-subtracted online softmax sum: score sc, values [x' | G u]
+__device__ __forceinline__ void h5_online(float sc, float4 xv, float4 gv, float& m, float& sw, float sa[8]) {
+    if (sc > m) {
+        const float r = __expf(m - sc);  // 0 when m = -inf
+        sw *= r;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) selfc[a] = 3 * it + a < n0 ? h.i0[3 * it + a] : -2;
-    f32x2 d2[3][NP];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int q = 0; q < NP; ++q) d2[a][q] = 0ull;
-    for (int l4 = 0; l4 < nyq; ++l4) {
-        float4 ua[3];
-        f32x2 vp[NP][4];  // pair q, component c (4 l4 + c of u): {candidate p, candidate p + 32}
-#pragma unroll
-        for (int a = 0; a < 3; ++a) ua[a] = *reinterpret_cast<const float4*>(&h.UI[3 * it + a][4 * l4]);
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            const float* row = &h.p2.Vp[vb_][jq + L * q][2 * (4 + 4 * l4)];
-            const ulonglong2 v01 = *reinterpret_cast<const ulonglong2*>(row);
-            const ulonglong2 v23 = *reinterpret_cast<const ulonglong2*>(row + 4);
-            vp[q][0] = v01.x;
-            vp[q][1] = v01.y;
-            vp[q][2] = v23.x;
-            vp[q][3] = v23.y;
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float uc[4] = {ua[a].x, ua[a].y, ua[a].z, ua[a].w};
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const f32x2 u2 = f2_pack(uc[c], uc[c]);
-#pragma unroll
-                for (int q = 0; q < NP; ++q) {
-                    const f32x2 t = f2_sub(u2, vp[q][c]);
-                    d2[a][q] = f2_fma(t, t, d2[a][q]);
-                }
-            }
-        }
+        for (int k = 0; k < 8; ++k) sa[k] *= r;
+        m = sc;
     }
-    float d[3][R];  // candidate jq + L r: pair r mod NP... r = q (lane 0) or q + NP (lane 1)
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int q = 0; q < NP; ++q) f2_unpack(d2[a][q], d[a][q], d[a][q + NP]);
-    // the three members side by side: independent shuffle and exp chains
-    float sc[3][R], mx[3], mold[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        mx[a] = -INFINITY;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int j = jq + L * r;
-            const bool ok = j < n && c0 + j != selfc[a] && selfc[a] != -2;
-            sc[a][r] = ok ? -d[a][r] * ib : -INFINITY;
-            mx[a] = fmaxf(mx[a], sc[a][r]);
-        }
-        mold[a] = h.p2.mrow[3 * it + a];
-    }
-    const unsigned gmask = L == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) mx[a] = fmaxf(mx[a], __shfl_xor_sync(gmask, mx[a], o));
-    __syncwarp(gmask);  // every lane of the group has read the old maxima
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int i = 3 * it + a;
-        const float mnew = fmaxf(mold[a], mx[a]);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int j = jq + L * r;  // pair j & 31, lane j >> 5
-            h.p2.Wp[vb_][j & 31][2 * i + (j >> 5)] = sc[a][r] == -INFINITY ? 0.0f : __expf(sc[a][r] - mnew);
-        }
-        if (jq == 0) {
-            h.p2.scl[vb_][i] = mold[a] == -INFINITY ? 0.0f : __expf(mold[a] - mnew);
-            h.p2.mrow[i] = mnew;
-        }
-    }
+    const float w = __expf(sc - m);
+    sw += w;
+    sa[0] = __fmaf_rn(w, xv.x, sa[0]);
+    sa[1] = __fmaf_rn(w, xv.y, sa[1]);
+    sa[2] = __fmaf_rn(w, xv.z, sa[2]);
+    sa[3] = __fmaf_rn(w, xv.w, sa[3]);
+    sa[4] = __fmaf_rn(w, gv.x, sa[4]);
+    sa[5] = __fmaf_rn(w, gv.y, sa[5]);
+    sa[6] = __fmaf_rn(w, gv.z, sa[6]);
+    sa[7] = __fmaf_rn(w, gv.w, sa[7]);
 }
 
 // Not inlined: HQL runs for a small share of the patches, and as a function of its own its
@@ -1576,7 +1456,10 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
         o.hi = __shfl_xor_sync(0xffffffffu, kk.hi, 1);
         o.lo = __shfl_xor_sync(0xffffffffu, kk.lo, 1);
         kk = half ? df_add(o, kk) : df_add(kk, o);
-        if (half == 0) h.K[a][j] = kk;
+        if (half == 0) {
+            h.K[a][j] = kk;
+            h.Kf[a][j] = df_to_f(kk);
+        }
     }
     SK_PHASE(PH_CHOL);
 
@@ -1827,126 +1710,178 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
     __syncthreads();
     SK_PHASE(PH_H4);
 
-    // H5: leave-one-out predictions for i in I0 at beta* (Eqs. (11)-(12)).  Thread (i, g)
-    // owns member i over the candidates j = g (mod kG5): online max-subtracted softmax of
-    // -||u_i - u_j||^2 / (2 beta*) (j != i) and the weighted sums of [x'_j | u_j | 1].
+    // H5: leave-one-out predictions for i in I0 at beta* (Eqs. (11)-(12)): for each member i
+    // the online max-subtracted softmax of -||u_i - u_j||^2 / (2 beta*) over the candidates
+    // j != i, and the weighted sums of [x'_j | G u_j | 1].  The correction G (u_i - u~_i) of
+    // Eq. (11) is linear in u, and G u_j = G L^-1 (y_j - y0) = K (y_j - y0), so four columns
+    // of G u_j stand in for the 32 of u_j in the sums.  Each warp owns every 8th group of 32
+    // candidates and runs without CTA barriers until the merge:
+    //   candidate mode (lane = candidate j): y_j - y0, u_j = L^-1 (y_j - y0), K (y_j - y0)
+    //     and x'_j into the warp's buffer;
+    //   member mode (lane = member i < 32): the buffered candidates in turn, the squared
+    //     whitened distance in packed two-lane FP32 over coordinate pairs;
+    //   member 32 (|I0| = 33): each lane keeps the sums of its own candidates.
     float num = 0.0f, den = 0.0f;
     if (n0 > 0) {
         const float ib = P.inv2beta[bstar];
-        const int nyq = (ny + 3) >> 2;
-        const int ntrip = (n0 + 2) / 3;  // member triples with a real member
-        // sums: thread (ib4, kb, jg) owns members 4ib4..+3 x columns 4kb..+3 over candidates
-        // jg, jg + G, ... of each chunk; G candidate groups, as many as the threads allow
-        // live column quads of [x' | u | 1]: columns 0 .. 3 + ny, and the constant (quad 9)
-        const int kql = (4 + ny + 3) / 4, nkq = kql + (kql <= 9 ? 1 : 0);
-        const int tasks = ((n0 + 3) / 4) * nkq;
-        const int G = min(4, kThreads / tasks);
-        const int jg = tid / tasks, rr = tid - jg * tasks, ib4 = rr / nkq, kq = rr - ib4 * nkq;
-        const int kb = kq < kql ? kq : 9;
-        const bool ac_act = jg < G;
-        f32x2 acc2[4][4];  // lanes: candidate pairs' first and second halves
+        const int nbat = (M + 31) >> 5;
+        float(*wb)[kWb] = h.h5.Wb[wid];
+        const bool has32 = n0 > 32;
+        const int selfi = lane < n0 ? h.i0[lane] : -1;
+        const int self32 = has32 ? h.i0[32] : -1;
+        float m = -INFINITY, sw = 0.0f, sa[8];  // member mode: member `lane`
+        float m3 = -INFINITY, s3 = 0.0f, a3[8];  // member 32 over this lane's candidates
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int k = 0; k < 8; ++k) sa[k] = a3[k] = 0.0f;
+        for (int bt = wid; bt < nbat; bt += kWarps) {
+            const int j = 32 * bt + lane;
+            const bool live = j < M;
+            {   // candidate mode
+                const int base = live ? h.cand[j] : 0;
+                float e[32];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc2[a][q] = 0ull;
-        if (tid < kI0Pad) {
-            h.p2.mrow[tid] = -INFINITY;
-            if (tid >= n0)
-                for (int k = 0; k < 36; ++k) h.UI[tid][k] = 0.0f;
-        }
-        hql_stage(sm, 0, 0, min(kCh, M), shift);
-        // chunk c: [barrier] sums of chunk c-1 and whitening of chunk c [barrier] staging of
-        // chunk c+1 and the scores of chunk c
-        for (int ch = 0; ch <= nchunks; ++ch) {
-            const int buf = ch & 1, c0 = ch * kCh, n = min(kCh, M - c0);
-            __syncthreads();  // staged chunk and the previous chunk's weights visible
-            if (ch > 0 && ac_act) {  // weighted sums of [x' | u | 1] of chunk ch-1 (online)
-                const int pb = buf ^ 1, pn = min(kCh, M - c0 + kCh);
-                const float4 s4 = *reinterpret_cast<const float4*>(&h.p2.scl[pb][4 * ib4]);
-                const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+                for (int l = 0; l < 32; ++l)
+                    e[l] = (live && l < ny) ? (sm.S[base + h.off[l]] - shift) - h.ys[l] : 0.0f;
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const f32x2 s2 = f2_pack(sv[a], sv[a]);
+                for (int r4 = 0; r4 < 8; ++r4) {  // u = L^-1 e (lower triangular, zero past Ny)
+                    float u[4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc2[a][q] = f2_mul(acc2[a][q], s2);
+                    for (int t = 0; t < 4; ++t) {
+                        const int r = 4 * r4 + t;
+                        float acc = 0.0f;
+#pragma unroll
+                        for (int q = 0; q <= r4; ++q) {
+                            const float4 lv = *reinterpret_cast<const float4*>(&h.Linv[r][4 * q]);
+                            acc = __fmaf_rn(lv.x, e[4 * q], acc);
+                            acc = __fmaf_rn(lv.y, e[4 * q + 1], acc);
+                            acc = __fmaf_rn(lv.z, e[4 * q + 2], acc);
+                            acc = __fmaf_rn(lv.w, e[4 * q + 3], acc);
+                        }
+                        u[t] = acc;
+                    }
+                    *reinterpret_cast<float4*>(&wb[lane][12 + 4 * r4]) = make_float4(u[0], u[1], u[2], u[3]);
                 }
-                // candidate pairs (p, p + 32); past pn the weights are zero
-                const int npair = min(kCh / 2, pn);
-                for (int p = jg; p < npair; p += G) {
-                    const ulonglong2 w01 = *reinterpret_cast<const ulonglong2*>(&h.p2.Wp[pb][p][8 * ib4]);
-                    const ulonglong2 w23 = *reinterpret_cast<const ulonglong2*>(&h.p2.Wp[pb][p][8 * ib4 + 4]);
-                    const ulonglong2 v01 = *reinterpret_cast<const ulonglong2*>(&h.p2.Vp[pb][p][8 * kb]);
-                    const ulonglong2 v23 = *reinterpret_cast<const ulonglong2*>(&h.p2.Vp[pb][p][8 * kb + 4]);
-                    const f32x2 wv[4] = {w01.x, w01.y, w23.x, w23.y};
-                    const f32x2 vv[4] = {v01.x, v01.y, v23.x, v23.y};
+                float g[4];  // K e
 #pragma unroll
-                    for (int a = 0; a < 4; ++a)
+                for (int aa = 0; aa < 4; ++aa) {
+                    float g0 = 0.0f, g1 = 0.0f;
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) acc2[a][q] = f2_fma(wv[a], vv[q], acc2[a][q]);
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 kv = *reinterpret_cast<const float4*>(&h.Kf[aa][4 * q]);
+                        g0 = __fmaf_rn(kv.x, e[4 * q], g0);
+                        g1 = __fmaf_rn(kv.y, e[4 * q + 1], g1);
+                        g0 = __fmaf_rn(kv.z, e[4 * q + 2], g0);
+                        g1 = __fmaf_rn(kv.w, e[4 * q + 3], g1);
+                    }
+                    g[aa] = g0 + g1;
+                }
+                float x[4];
+#pragma unroll
+                for (int aa = 0; aa < 4; ++aa)
+                    x[aa] = live ? sm.S[base + (aa >> 1) * kReg + (aa & 1) + 2 * kReg + 2] - shift : 0.0f;
+                *reinterpret_cast<float4*>(&wb[lane][0]) = make_float4(x[0], x[1], x[2], x[3]);
+                *reinterpret_cast<float4*>(&wb[lane][4]) = make_float4(g[0], g[1], g[2], g[3]);
+                if (has32 && live && j != self32) {  // member 32 against this candidate
+                    f32x2 d2 = 0ull;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(&wb[lane][12 + 4 * q]);
+                        const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(&h.UI[32][4 * q]);
+                        f32x2 t = f2_sub(w.x, v.x);
+                        d2 = f2_fma(t, t, d2);
+                        t = f2_sub(w.y, v.y);
+                        d2 = f2_fma(t, t, d2);
+                    }
+                    float dl, dh;
+                    f2_unpack(d2, dl, dh);
+                    h5_online(-(dl + dh) * ib, make_float4(x[0], x[1], x[2], x[3]),
+                              make_float4(g[0], g[1], g[2], g[3]), m3, s3, a3);
                 }
             }
-            if (ch == nchunks) break;
-            {   // warp w: coordinate groups (w & 3, 7 - (w & 3)) of candidates 32 (w >> 2) + lane
-                const int qw = wid & 3, jw = lane + 32 * (wid >> 2);
-                float ua[4], ub[4];
-                whiten_quads(h, buf, ny, jw, qw, ua, ub);
-                float* vrow = &h.p2.Vp[buf][lane][wid >> 2];  // column k at vrow[2 k]
+            __syncwarp();
+            if (lane < n0) {  // member mode
+                f32x2 U[16];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    vrow[2 * (4 + 4 * qw + r)] = ua[r];
-                    vrow[2 * (4 + 4 * (7 - qw) + r)] = ub[r];
+                for (int q = 0; q < 8; ++q) {
+                    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(&h.UI[lane][4 * q]);
+                    U[2 * q] = v.x;
+                    U[2 * q + 1] = v.y;
                 }
-                if (qw == 0) {
+                const int nc = min(32, M - 32 * bt);
+                for (int c = 0; c < nc; ++c) {
+                    f32x2 d2 = 0ull;
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) vrow[2 * r] = h.Z[buf][jw][r];
-                } else if (qw == 1) {
-                    vrow[2 * 36] = h.Z[buf][jw][36];
-#pragma unroll
-                    for (int r = 37; r < 40; ++r) vrow[2 * r] = 0.0f;
+                    for (int q = 0; q < 8; ++q) {
+                        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(&wb[c][12 + 4 * q]);
+                        f32x2 t = f2_sub(U[2 * q], v.x);
+                        d2 = f2_fma(t, t, d2);
+                        t = f2_sub(U[2 * q + 1], v.y);
+                        d2 = f2_fma(t, t, d2);
+                    }
+                    if (32 * bt + c == selfi) continue;
+                    float dl, dh;
+                    f2_unpack(d2, dl, dh);
+                    h5_online(-(dl + dh) * ib, *reinterpret_cast<const float4*>(&wb[c][0]),
+                              *reinterpret_cast<const float4*>(&wb[c][4]), m, sw, sa);
                 }
             }
-            __syncthreads();
-            SK_PHASE(PH_X1);
-            if (ch + 1 < nchunks) hql_stage(sm, buf ^ 1, c0 + kCh, min(kCh, M - c0 - kCh), shift);
-            // squared whitened distances, scores, chunk maxima and weights (Eq. (12) with
-            // candidate i left out)
-            if (ntrip <= 8) h5_scores<32>(h, buf, n0, nyq, n, c0, ib);
-            else h5_scores<16>(h, buf, n0, nyq, n, c0, ib);
-            SK_PHASE(PH_X2);
+            __syncwarp();  // the buffer takes the next group
         }
-        __syncthreads();  // Vp / Wp no longer needed: their storage takes the partial sums
-        if (ac_act) {
+        // the warps' partial sums: member mode, and member 32 reduced over the lanes
+        if (lane < n0) {
+            float* mg = h.h5.Mg[wid][lane];
+            mg[0] = m;
+            mg[1] = sw;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                float acc[4];
+            for (int k = 0; k < 8; ++k) mg[2 + k] = sa[k];
+        }
+        if (has32) {
+            float wm = m3;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float lo, hi;
-                    f2_unpack(acc2[a][q], lo, hi);
-                    acc[q] = lo + hi;
-                }
-                *reinterpret_cast<float4*>(&h.p2.accP[jg][4 * ib4 + a][4 * kb]) =
-                    make_float4(acc[0], acc[1], acc[2], acc[3]);
+            for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+            const float sc = m3 == -INFINITY ? 0.0f : __expf(m3 - wm);
+            float v9[9];
+            v9[0] = s3 * sc;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v9[1 + k] = a3[k] * sc;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int k = 0; k < 9; ++k) v9[k] += __shfl_xor_sync(0xffffffffu, v9[k], o);
+            if (lane == 0) {
+                float* mg = h.h5.Mg[wid][32];
+                mg[0] = wm;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) mg[1 + k] = v9[k];
             }
         }
         __syncthreads();
-        for (int idx = tid; idx < n0 * 37; idx += kThreads) {
-            const int i = idx / 37, k = idx - (idx / 37) * 37;
-            if (k >= 4 + ny && k < 36) continue;  // (columns past the context: not computed)
-            float a = h.p2.accP[0][i][k];
-            for (int g = 1; g < G; ++g) a += h.p2.accP[g][i][k];
-            h.accI[i][k] = a;
+        // merge over the warps: accI[i] = x' sums (0..3), G u sums (4..7), weight sum (8)
+        for (int idx = tid; idx < n0 * 9; idx += kThreads) {
+            const int i = idx / 9, k = idx - (idx / 9) * 9;
+            float mx = -INFINITY;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) mx = fmaxf(mx, h.h5.Mg[w][i][0]);
+            const int col = k == 8 ? 1 : 2 + k;
+            float acc = 0.0f;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const float mw = h.h5.Mg[w][i][0];
+                if (mw != -INFINITY) acc = __fmaf_rn(__expf(mw - mx), h.h5.Mg[w][i][col], acc);
+            }
+            h.accI[i][k] = acc;
         }
         __syncthreads();
-        // r_i = x_i - x~_i ; g_i = G (u_i - u~_i) ; alpha = sum r.g / sum g.g
+        // r_i = x_i - x~_i ; g_i = G u_i - (sum_j w_ij G u_j) / sum_j w_ij ;
+        // alpha = sum r.g / sum g.g
         if (tid < 4 * kMaxI0) {
-            const int i = tid >> 2, a = tid & 3;
+            const int i = tid >> 2, aa = tid & 3;
             if (i < n0) {
-                const float inv = 1.0f / h.accI[i][36];
-                const float r = h.XI[i][a] - h.accI[i][a] * inv;
-                float gg = 0.0f;
-                for (int k = 0; k < ny; ++k)
-                    gg = __fmaf_rn(h.G[a][k], h.UI[i][k] - h.accI[i][4 + k] * inv, gg);
+                const float inv = 1.0f / h.accI[i][8];
+                const float r = h.XI[i][aa] - h.accI[i][aa] * inv;
+                float gu = 0.0f;
+                for (int k = 0; k < ny; ++k) gu = __fmaf_rn(h.G[aa][k], h.UI[i][k], gu);
+                const float gg = gu - h.accI[i][4 + aa] * inv;
                 num = r * gg;
                 den = gg * gg;
             }

@@ -440,8 +440,7 @@ __device__ __forceinline__ int select_patch(const Smem& sm, int lane) {
             best = max(best, cnt * 64 + (63 - p));
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    best = __reduce_max_sync(0xffffffffu, best);
     return 63 - (best & 63);
 }
 
@@ -451,9 +450,12 @@ struct CtxStats {
 };
 
 // context of the window at (wr, wc): size, flatness and mean.  Warp-level reductions; every
-// lane returns the same values.
+// lane returns the same values.  Support values lie in [0, 255] (clipped estimates, 8-bit
+// pixels), where the order of the FP32 bit patterns (with -0 folded to +0) is the order of
+// the values: the maximum and minimum are single integer warp reductions.
 __device__ __forceinline__ CtxStats ctx_stats(const Smem& sm, int wr, int wc, int lane) {
-    float mx = -INFINITY, mn = INFINITY, sum = 0.0f;
+    unsigned mxb = 0u, mnb = 0xFFFFFFFFu;
+    float sum = 0.0f;
     unsigned bal[2];
 #pragma unroll
     for (int h2 = 0; h2 < 2; ++h2) {  // window position k of this lane: its availability bit
@@ -464,21 +466,20 @@ __device__ __forceinline__ CtxStats ctx_stats(const Smem& sm, int wr, int wc, in
         bal[h2] = __ballot_sync(0xffffffffu, on);
         if (on) {
             const float v = sm.S[(wr + r) * kReg + wc + c];
-            mx = fmaxf(mx, v);
-            mn = fminf(mn, v);
+            const unsigned b = __float_as_uint(v + 0.0f);  // -0 -> +0
+            mxb = max(mxb, b);
+            mnb = min(mnb, b);
             sum += v;
         }
     }
     const unsigned long long ymask = (unsigned long long)bal[0] | ((unsigned long long)bal[1] << 32);
+    mxb = __reduce_max_sync(0xffffffffu, mxb);
+    mnb = __reduce_min_sync(0xffffffffu, mnb);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    }
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     CtxStats cs;
     cs.ny = __popcll(ymask);
-    cs.phi = mx - mn;
+    cs.phi = cs.ny > 0 ? __uint_as_float(mxb) - __uint_as_float(mnb) : 0.0f;
     cs.mean = cs.ny > 0 ? sum / (float)cs.ny : 0.0f;
     return cs;
 }

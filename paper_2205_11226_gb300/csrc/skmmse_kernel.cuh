@@ -543,19 +543,18 @@ __device__ __forceinline__ IdlOut idl_step(const KParams& P, int wr, int wc,
                        s0, sx);
             ++cnt;
         }
-        // warp combine: the maximum first, then one rescale per lane and plain sums
-        float wm = m;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+        // warp combine: the maximum first, then one rescale per lane and plain sums.  The
+        // scores are <= 0 (or kNegBig): with the sign bit forced, their bit patterns order
+        // inversely to the values, so the maximum is one unsigned minimum reduction.
+        const float wm = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(m) | 0x80000000u));
         const float lsc = __expf(m - wm);
         float ws = s0 * lsc, wx[4] = {sx[0] * lsc, sx[1] * lsc, sx[2] * lsc, sx[3] * lsc};
-        int wc = cnt;
+        const int wc = __reduce_add_sync(0xffffffffu, cnt);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             ws += __shfl_xor_sync(0xffffffffu, ws, o);
 #pragma unroll
             for (int q = 0; q < 4; ++q) wx[q] += __shfl_xor_sync(0xffffffffu, wx[q], o);
-            wc += __shfl_xor_sync(0xffffffffu, wc, o);
         }
         IdlSlot* slot = &sm.idl[k & 1][0];
         if (lane == 0) {

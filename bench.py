@@ -334,12 +334,19 @@ def compare_legs(ctx, skmmse, args, frames, masks, fd, md, od, p_main, ms_main, 
     ctx.conceal_batch(fd, md, p_main, outs=od, stream=stream)
     ctx.conceal_batch(fd, md, p32, outs=o32, stream=stream)
     torch.cuda.synchronize()
-    dpsnr, dmax = 0.0, 0
+    dframes, dmax = [], 0
+    se = {"main": 0.0, "fp32": 0.0}
+    npx = 0
     for i in range(len(frames)):
         lm = synth.lost_pixel_mask(masks[i], frames[i].shape[1], frames[i].shape[0])
         a, b = od[i].cpu().numpy(), o32[i].cpu().numpy()
-        dpsnr = max(dpsnr, abs(synth.psnr(a, frames[i], lm) - synth.psnr(b, frames[i], lm)))
+        dframes.append(abs(synth.psnr(a, frames[i], lm) - synth.psnr(b, frames[i], lm)))
         dmax = max(dmax, int(np.abs(a.astype(np.int32) - b.astype(np.int32)).max()))
+        ref = frames[i][lm].astype(np.float64)
+        se["main"] += float(np.sum((a[lm] - ref) ** 2))
+        se["fp32"] += float(np.sum((b[lm] - ref) ** 2))
+        npx += int(lm.sum())
+    pooled = {k: 10.0 * np.log10(255.0 ** 2 / (v / npx)) for k, v in se.items()}
     # one 1920x1080 frame (runs of 4-20 lost blocks to 20 %, fine texture), one call per frame
     f1, m1 = synth.workload_slice_1080p(args.seed)
     f1d, m1d = torch.from_numpy(f1).cuda(), torch.from_numpy(m1).cuda()
@@ -355,7 +362,10 @@ def compare_legs(ctx, skmmse, args, frames, masks, fd, md, od, p_main, ms_main, 
             "frames_1080p_per_s": fps,
             "frames_1080p_workload": "1920x1080, runs of 4-20 lost blocks to 20 %, fine texture, "
                                      f"{int(m1.sum())} lost blocks, one call per frame",
-            "psnr_delta_db_vs_fp32_max_frame": dpsnr,
+            # free-running: a near-tie decision that flips moves its whole dependency chain
+            "psnr_delta_db_vs_fp32_max_frame": max(dframes),
+            "psnr_delta_db_vs_fp32_median_frame": float(np.median(dframes)),
+            "psnr_delta_db_vs_fp32_pooled": abs(pooled["main"] - pooled["fp32"]),
             "max_abs_diff_gray_vs_fp32_uint8": dmax}
 
 

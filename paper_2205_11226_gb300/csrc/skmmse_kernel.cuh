@@ -176,8 +176,8 @@ struct __align__(16) Hql {
     df32 corr[4];
     float red[kWarps][4];
     int scan[kWarps + 1];
-    int hist[256];
-    int sel[4];
+    int hist[2][256];  // I0 radix select: this pass's histogram, the next pass's cleared
+    int sel[2][2];
     int colNi[36];
     float colF[36];
     int koff[kZs];
@@ -1623,12 +1623,12 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
     if (n0 > 0) {
         unsigned prefix = 0, maskbits = 0;
         int need = n0;
-        for (int shiftb = 24; shiftb >= 0; shiftb -= 8) {
-            for (int i = tid; i < 256; i += kThreads) h.hist[i] = 0;
-            __syncthreads();
+        for (int i = tid; i < 256; i += kThreads) h.hist[0][i] = 0;
+        __syncthreads();
+        for (int shiftb = 24, pb = 0; shiftb >= 0; shiftb -= 8, pb ^= 1) {
             for (int j = tid; j < M; j += kThreads) {
                 const unsigned key = __float_as_uint(h.d[j]);
-                if ((key & maskbits) == prefix) atomicAdd(&h.hist[(key >> shiftb) & 255u], 1);
+                if ((key & maskbits) == prefix) atomicAdd(&h.hist[pb][(key >> shiftb) & 255u], 1);
             }
             __syncthreads();
             if (wid == 0) {
@@ -1636,7 +1636,7 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
                 int loc[8], s8 = 0;
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    loc[q] = h.hist[lane * 8 + q];
+                    loc[q] = h.hist[pb][lane * 8 + q];
                     s8 += loc[q];
                 }
                 int incl = s8;
@@ -1657,15 +1657,16 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
                         }
                         acc += loc[q];
                     }
-                    h.sel[0] = dg;
-                    h.sel[1] = need - acc;
+                    h.sel[pb][0] = dg;
+                    h.sel[pb][1] = need - acc;
                 }
+            } else {  // the next pass's histogram (its last reader was two barriers ago)
+                for (int i = tid - 32; i < 256; i += kThreads - 32) h.hist[pb ^ 1][i] = 0;
             }
             __syncthreads();
-            prefix |= (unsigned)h.sel[0] << shiftb;
+            prefix |= (unsigned)h.sel[pb][0] << shiftb;
             maskbits |= 255u << shiftb;
-            need = h.sel[1];
-            __syncthreads();
+            need = h.sel[pb][1];
         }
         // members: key < prefix, plus the first `need` with key == prefix (index order)
         unsigned f = 0, eqf = 0;

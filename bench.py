@@ -269,15 +269,15 @@ def unit_rooflines(skmmse, st, n_lost, frames, mean_ms, precision, stream):
       candidate for the beta grid, |I0| per HQL candidate for the leave-one-out pass)
       against the probed exp2 rate;
     - tensor: MMA operations issued by the HQL contractions (per 64-candidate chunk:
-      covariance 24 MMAs of 128x48x16, distances 6 of 128x32x16, beta sums 12 of
-      128x48x16) against the measured dense BF16 rate (FP16 runs at the same rate);
+      covariance 16 MMAs of 64x48x16, distances 6 of 64x32x16, beta sums 12 of 64x48x16)
+      against the measured dense BF16 rate (FP16 runs at the same rate);
     - hbm: frame bytes read and written per step against the measured copy bandwidth."""
     pk = skmmse.probe_peaks(stream)
     peaks, src = measured_peaks_file()
     sec = mean_ms * 1e-3
     exps = st["idl_cand_evals"] + st["n_beta"] * st["hql_cands"] + st["hql_i0_cands"]
     chunks = st["hql_cands"] / 64.0 + 0.5 * st["n_hql"]
-    mma = chunks * (24 * 2 * 128 * 48 * 16 + 6 * 2 * 128 * 32 * 16 + 12 * 2 * 128 * 48 * 16)
+    mma = chunks * (16 * 2 * 64 * 48 * 16 + 6 * 2 * 64 * 32 * 16 + 12 * 2 * 64 * 48 * 16)
     if precision == "fp32":
         mma = 0.0
     hbm_bytes = 2 * sum(f.size for f in frames) + n_lost * (256 * 4 * 2)

@@ -78,10 +78,10 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Tensor-memory lane of row r of an M = 64 accumulator (cta_group::1): 16 rows in the first
-// half of each warp's 32-lane quarter (rows 16w .. 16w+15 in lanes 32w .. 32w+15); the
-// columns are those of D.  (An M = 128 accumulator keeps row r in lane r.)
-__host__ __device__ __forceinline__ int m64_lane(int r) { return ((r >> 4) << 5) | (r & 15); }
+// Accumulator layouts (cta_group::1): an M = 128 accumulator keeps row r in lane r; an
+// M = 64 accumulator keeps 16 rows in the first half of each warp's 32-lane quarter, rows
+// 16w .. 16w+15 in lanes 32w .. 32w+15, so warp w reads row 16w + lane for lane < 16.  The
+// columns are those of D.
 
 // the calling warp reads 8 consecutive 32-bit columns of its 32 TMEM lanes
 // (warp w of the CTA owns lanes 32*(w%4) .. 32*(w%4)+31)

@@ -241,6 +241,57 @@ def test_nu_bounded_by_candidate_count():
     assert np.all(t["log_nu"][sel] <= np.log(np.maximum(t["m"][sel], 1)) + 1e-12)
 
 
+def numpy_idl(R, A, pr, pc, p):
+    """Independent NumPy statement of one IDL decision and estimate (Eqs. (15), (18),
+    readings R5/R6) for the patch with top-left (pr, pc) of a 48x48 region R with
+    availability A: the support grows ring by ring (Chebyshev distance of the candidate
+    patch from x0 at most ring_step * k) until the sum of raw weights reaches T_nu.
+    Returns (layer, rings evaluated, log nu, estimate or None, M)."""
+    wr, wc = pr - 2, pc - 2
+    cfg = [(r, c) for r in range(6) for c in range(6)
+           if A[wr + r, wc + c] and not (r in (2, 3) and c in (2, 3))]
+    ny = len(cfg)
+    y0 = np.array([R[wr + r, wc + c] for r, c in cfg])
+    xcfg = [(2, 2), (2, 3), (3, 2), (3, 3)]
+    cands = brute_candidates(A, cfg + xcfg)
+    X = np.array([[R[u + r, v + c] for r, c in xcfg] for u, v in cands])
+    Y = np.array([[R[u + r, v + c] for r, c in cfg] for u, v in cands])
+    D = np.array([max(abs(u + 2 - pr), abs(v + 2 - pc)) for u, v in cands])
+    w = np.exp(-np.sum((Y - y0) ** 2, axis=1) / (2 * p.sigma2 * ny))
+    k = 0
+    while True:
+        k += 1
+        inner = D <= p.ring_step * k
+        nu = w[inner].sum()
+        if nu >= p.t_nu:
+            return oracle.IDL, k, np.log(nu), w[inner] @ X[inner] / nu, len(cands)
+        if inner.all():
+            return oracle.HQL, k, np.log(nu), None, len(cands)
+
+
+# (profile, sigma^2, frame seed) -> accepted ring (0: no ring reaches T_nu, HQL)
+IDL_CASES = [("express", 10.0, 1, 1), ("efficient", 3.0, 2, 2), ("efficient", 3.0, 8, 3),
+             ("excellent", 3.0, 3, 5), ("excellent", 10.0, 7, 2), ("efficient", 3.0, 4, 0),
+             ("excellent", 10.0, 1, 0)]
+
+
+@pytest.mark.parametrize("profile,sigma2,seed,ring", IDL_CASES)
+def test_idl_first_patch_matches_numpy_brute_force(profile, sigma2, seed, ring):
+    # the default aperture and a narrower one, rings 1 to 5 and the fall-through to HQL:
+    # the ring partition, the 2 sigma^2 Ny normalisation and the T_nu test all show
+    f = synth.make_frame(128, 128, seed, fine_texture=seed % 2 == 0)
+    m = isolated(f, 3, 3)
+    p = oracle.params(profile, t_phi=-1.0, sigma2=sigma2)
+    t0 = oracle.conceal(f, m, p, trace=True)["trace"][0, 0]
+    R, A = region_avail_first_step(f, 3, 3)
+    layer, k, log_nu, x, M = numpy_idl(R, A, 16, 16, p)
+    assert (layer == oracle.IDL) == (ring > 0) and (k == ring or ring == 0)
+    assert t0["layer"] == layer and t0["ring"] == k and t0["m"] == M
+    assert abs(t0["log_nu"] - log_nu) < 1e-9
+    if x is not None:
+        assert np.max(np.abs(t0["x"] - x)) < 1e-9
+
+
 # ---------------------------------------------------------------------------------------
 # HQL, Eq. (13)
 

@@ -179,6 +179,22 @@ def test_brl_first_patch_is_context_mean():
     assert abs(r["out"][48, 48] - win.mean()) < 1e-12
 
 
+@pytest.mark.parametrize("top,layer_is_brl", [(120, True), (121, False)])
+def test_brl_iff_flatness_at_most_t_phi(top, layer_is_brl):
+    # Eq. (17) phi = max - min of the context; R4: BRL iff phi <= T_phi, so the integer tie
+    # phi = T_phi = 20 (Efficient, Table I) is BRL and phi = 21 is not
+    rng = np.random.default_rng(12)
+    f = rng.integers(101, 120, size=(128, 128)).astype(np.uint8)
+    f[46, 46], f[46, 47] = 100, top  # in the context of patch (0,0) of block (3,3)
+    p = oracle.params("efficient")
+    assert p.t_phi == 20.0
+    t0 = oracle.conceal(f, isolated(f, 3, 3), p, trace=True)["trace"][0, 0]
+    R, A = region_avail_first_step(f, 3, 3)
+    win = R[14:20, 14:20][A[14:20, 14:20]]
+    assert t0["patch"] == 0 and t0["phi"] == win.max() - win.min() == top - 100
+    assert (t0["layer"] == oracle.BRL) == layer_is_brl
+
+
 def test_no_candidate_falls_back_to_brl():
     # 18x16 frame: the only support of the lost block is a 2-row strip, too thin for any
     # candidate (x rows plus context rows need 4 available rows)

@@ -885,9 +885,15 @@ __device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, int nz, float 
     // at the zeros the pass started from.  Row slot ri < nz is feature ri, slot nz the
     // constant.  A quarter-warp writes one 16-byte column group of 8 consecutive slots
     // (one 128-byte core matrix: no bank conflicts); one task per thread for nz <= 31.
+    // The second round of tasks (rows 32..36) goes to the first two warps, with the lanes
+    // of each 8-lane group in reverse order: the live ones (rows 32..36) then fall on lanes
+    // 3..7 of the group, where the beta pass with the default 25-value grid gives them no
+    // weight row (h3_mixed).
     const int nr = nz + 1;
-    const int ntask = ((nr + 7) >> 3) * 64;
-    for (int idx = threadIdx.x; idx < ntask; idx += kThreads) {
+    const int ntask = ((nr + 7) >> 3) * 64;  // nz <= 36: at most 5 row groups, 320 tasks
+    for (int rnd = 0; rnd < 2; ++rnd) {
+        const int idx = rnd == 0 ? (int)threadIdx.x : kThreads + ((int)threadIdx.x ^ 7);
+        if (idx >= ntask) continue;
         const int ri = ((idx >> 6) << 3) | (idx & 7), g8 = (idx >> 3) & 7;
         if (ri >= nr) continue;
         const int a = ri < nz ? ri : 36;
@@ -1104,9 +1110,11 @@ __device__ __noinline__ void h3_mixed(const KParams& P, int M, int nz, float shi
         stage_zt<BF16, false>(sm, c0, n, nz, shift, zt(bf, 0), zt(bf, 1), nullptr);
         // A = W (rows: beta, columns: candidates), 32 rows x 8 column groups; a quarter-warp
         // stores 8 consecutive rows of one column group (conflict-free)
-        {  // one task per thread
+        {  // one task per thread; rows 24..31 (of which only 24 is live with the default
+           // 25-value grid) go to the first two warps, which take the second round of Z'
+           // tasks on other lanes (stage_zt), so that no thread stages three rows
             const int q = tid;
-            const int b = (q & 7) | ((q >> 6) << 3), g8 = (q >> 3) & 7;
+            const int b = (q & 7) | (((q >> 6) ^ 3) << 3), g8 = (q >> 3) & 7;
             if (b < nb) {
                 float v[8];
                 const float ib = P.inv2beta[b];

@@ -1195,6 +1195,38 @@ __device__ __forceinline__ void h5_online(float sc, float4 xv, float4 gv, float&
     sa[7] = __fmaf_rn(w, gv.w, sa[7]);
 }
 
+// member mode of the leave-one-out pass for one buffered group of nc candidates: the
+// squared whitened distance of member u (its first NQ coordinate groups; the rest are
+// zero) to each candidate, in packed two-lane FP32, and the online sums; cself is the
+// member's own index in the group (skipped), or out of range
+template <int NQ>
+__device__ __forceinline__ void h5_members(const float (*wb)[kWb], const float* ui, int nc, int cself,
+                                           float ib, float& m, float& sw, float sa[8]) {
+    f32x2 U[2 * NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(&ui[4 * q]);
+        U[2 * q] = v.x;
+        U[2 * q + 1] = v.y;
+    }
+    for (int c = 0; c < nc; ++c) {
+        f32x2 d2 = 0ull;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(&wb[c][12 + 4 * q]);
+            f32x2 t = f2_sub(U[2 * q], v.x);
+            d2 = f2_fma(t, t, d2);
+            t = f2_sub(U[2 * q + 1], v.y);
+            d2 = f2_fma(t, t, d2);
+        }
+        if (c == cself) continue;
+        float dl, dh;
+        f2_unpack(d2, dl, dh);
+        h5_online(-(dl + dh) * ib, *reinterpret_cast<const float4*>(&wb[c][0]),
+                  *reinterpret_cast<const float4*>(&wb[c][4]), m, sw, sa);
+    }
+}
+
 // Not inlined: HQL runs for a small share of the patches, and as a function of its own its
 // register demand does not spill the per-step loop of the kernel.
 // The arguments are scalars (the window position, the context mask and size, the context
@@ -1734,6 +1766,10 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
     if (n0 > 0) {
         const float ib = P.inv2beta[bstar];
         const int nbat = (M + 31) >> 5;
+        // whitened coordinates in groups of 4: past Ny they are exact zeros (L^-1 and the
+        // members' u_i are zero there), so member mode sums only the first nq groups, with
+        // the results of all 8 bit for bit
+        const int nq = (ny + 3) >> 2;
         float(*wb)[kWb] = h.h5.Wb[wid];
         const bool has32 = n0 > 32;
         const int selfi = lane < n0 ? h.i0[lane] : -1;
@@ -1808,31 +1844,11 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
                 }
             }
             __syncwarp();
-            if (lane < n0) {  // member mode
-                f32x2 U[16];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(&h.UI[lane][4 * q]);
-                    U[2 * q] = v.x;
-                    U[2 * q + 1] = v.y;
-                }
+            if (lane < n0) {  // member mode, unrolled over the live coordinate groups
                 const int nc = min(32, M - 32 * bt);
-                for (int c = 0; c < nc; ++c) {
-                    f32x2 d2 = 0ull;
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(&wb[c][12 + 4 * q]);
-                        f32x2 t = f2_sub(U[2 * q], v.x);
-                        d2 = f2_fma(t, t, d2);
-                        t = f2_sub(U[2 * q + 1], v.y);
-                        d2 = f2_fma(t, t, d2);
-                    }
-                    if (32 * bt + c == selfi) continue;
-                    float dl, dh;
-                    f2_unpack(d2, dl, dh);
-                    h5_online(-(dl + dh) * ib, *reinterpret_cast<const float4*>(&wb[c][0]),
-                              *reinterpret_cast<const float4*>(&wb[c][4]), m, sw, sa);
-                }
+                if (nq <= 4) h5_members<4>(wb, h.UI[lane], nc, selfi - 32 * bt, ib, m, sw, sa);
+                else if (nq <= 5) h5_members<5>(wb, h.UI[lane], nc, selfi - 32 * bt, ib, m, sw, sa);
+                else h5_members<8>(wb, h.UI[lane], nc, selfi - 32 * bt, ib, m, sw, sa);
             }
             __syncwarp();  // the buffer takes the next group
         }

@@ -140,6 +140,32 @@ def test_threads_and_sampling_are_exact():
     assert np.array_equal(c[blk], a[blk])
 
 
+@pytest.mark.parametrize("support", [0, 1])
+def test_support_rule_r1(support):
+    # R1: block A = (3,3) is concealed before its right neighbour B = (3,4) (raster order);
+    # with concealed_is_support = 1 B reads A's concealed pixels, with 0 only received
+    # ones.  Received pixels of block column 2 lie in A's 48x48 region but not in B's:
+    # changing them changes A, and B only through A (support = 1).  Block column 5 lies in
+    # B's region only: it never changes A, which is concealed first.
+    f = synth.make_frame(128, 128, 3, fine_texture=True)
+    m = np.zeros((8, 8), np.uint8)
+    m[3, 3] = m[3, 4] = 1
+    p = oracle.params("efficient", concealed_is_support=support)
+    A, B = (slice(48, 64), slice(48, 64)), (slice(48, 64), slice(64, 80))
+    base = oracle.conceal(f, m, p)["out"]
+    rng = np.random.default_rng(1)
+    g = f.copy()
+    g[32:80, 32:48] = rng.integers(0, 256, size=(48, 16))
+    a = oracle.conceal(g, m, p)["out"]
+    assert np.abs(a[A] - base[A]).max() > 1.0
+    assert (np.abs(a[B] - base[B]).max() > 1e-3) == (support == 1)
+    g = f.copy()
+    g[32:80, 80:96] = rng.integers(0, 256, size=(48, 16))
+    b = oracle.conceal(g, m, p)["out"]
+    assert np.array_equal(b[A], base[A])
+    assert np.abs(b[B] - base[B]).max() > 1.0
+
+
 def test_rejects_odd_sizes():
     with pytest.raises(ValueError):
         oracle.conceal(np.zeros((33, 32), np.uint8), np.ones((3, 2), np.uint8))

@@ -412,6 +412,23 @@ def test_hql_first_patch_matches_numpy_brute_force(seed):
     assert np.max(np.abs(np.clip(xhat, 0, 255) - t0["x"])) < 1e-8
 
 
+@pytest.mark.parametrize("seed", [22, 39])
+def test_hql_estimate_is_clipped_to_the_pixel_range(seed):
+    # R8: Eq. (13) can extrapolate past [0, 255] on a high-contrast frame (here above 255
+    # for seed 22, below 0 for seed 39); the estimate and the output are clipped
+    base = synth.make_frame(128, 128, seed, fine_texture=True).astype(np.int32)
+    f = np.clip(base * 2 - 60, 0, 255).astype(np.uint8)
+    p = oracle.params("efficient", t_phi=-1.0, t_nu=1e300)
+    r = oracle.conceal(f, isolated(f, 3, 3), p, trace=True)
+    t0 = r["trace"][0, 0]
+    R, A = region_avail_first_step(f, 3, 3)
+    xhat = numpy_hql(R, A, 16, 16, p)[0]
+    assert t0["layer"] == oracle.HQL and t0["patch"] == 0
+    assert xhat.max() > 255.5 or xhat.min() < -0.5
+    assert np.max(np.abs(t0["x"] - np.clip(xhat, 0, 255))) < 1e-8
+    assert np.array_equal(r["out"][48:50, 48:50].reshape(-1), t0["x"])
+
+
 # ---------------------------------------------------------------------------------------
 # In-loop 8-bit quantisation (variant of R8): estimates are written back rounded
 

@@ -393,7 +393,8 @@ def numpy_hql(R, A, pr, pc, p):
     alphas = np.linspace(-0.5, 1.5, 20001)
     epsx = [np.mean(np.sum((R_ - a * G_) ** 2, axis=1)) for a in alphas]
     a_scan = float(np.clip(alphas[int(np.argmin(epsx))], 0, 1))
-    a_cf = float(np.clip(np.sum(R_ * G_) / np.sum(G_ * G_), 0, 1))
+    den = np.sum(G_ * G_)  # 0: every alpha minimises Eq. (11); R7 takes 0
+    a_cf = float(np.clip(np.sum(R_ * G_) / den, 0, 1)) if den > 0 else 0.0
     return xt + a_cf * K @ (y0 - yt), a_cf, a_scan, bi, len(cands)
 
 

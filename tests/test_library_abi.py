@@ -63,3 +63,34 @@ def test_null_arguments_rejected_without_compute(lib):
     lib.skmmse_destroy(None)
     assert lib.skmmse_status_str(6) == b"dependency wait timed out on the device"
     assert lib.skmmse_status_str(99) == b"unknown status"
+
+
+def test_argument_validation_before_any_device_call(lib):
+    # skmmse_conceal_noalloc checks its parameters and frame on the host before its first
+    # CUDA call, so every rejection below is reached without a GPU.  The device pointers
+    # are placeholders that are never dereferenced.
+    FR, MB, OUT = 0x10000, 0x20000, 0x30000
+
+    def call(w=64, h=64, pitch=64, out_pitch=64, f32=None, mb=MB, **kw):
+        p = skmmse.params()
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return lib.skmmse_conceal_noalloc(FR, w, h, pitch, mb, ctypes.byref(p), OUT, out_pitch,
+                                          f32, None, None)
+
+    ARG, SHAPE, ALIGN, TOO_LARGE = 1, 2, 3, 8
+    assert call(t_nu=0.0) == ARG
+    assert call(sigma2=-1.0) == ARG
+    assert call(t_phi=float("nan")) == ARG
+    assert call(ridge_rel=-1e-3) == ARG
+    assert call(ring_step=0) == ARG
+    assert call(beta_kmin=3, beta_kmax=2) == ARG
+    assert call(beta_kmin=-40, beta_kmax=40) == ARG      # more grid values than supported
+    assert call(precision=7) == ARG
+    assert call(flags=1 << 20) == ARG
+    assert call(flags=skmmse.FLAG_TRACE) == ARG         # no trace buffer on this entry
+    assert call(mb=None) == ARG
+    assert call(w=63) == SHAPE and call(h=0) == SHAPE
+    assert call(pitch=32) == SHAPE and call(out_pitch=32) == SHAPE
+    assert call(f32=OUT + 2) == ALIGN
+    assert call(w=4096, h=4096, pitch=4096, out_pitch=4096) == TOO_LARGE

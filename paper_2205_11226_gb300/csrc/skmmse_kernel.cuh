@@ -850,7 +850,8 @@ __device__ __forceinline__ void mma3(uint32_t tmem, const uint16_t* ahi, const u
 // The chunk pipeline of a pass: [tiles_ready] issue the MMAs of chunk c, stage chunk c + 1
 // into the other buffer, [mma_wait] chunk c complete.  Issuing an MMA stalls the issuing
 // thread until the tensor core takes it; the issuer is lane 0 of the last warp, whose
-// threads take one staging task each (the second round of tasks goes to the first warps).
+// threads take one Z' staging task each (the second round of Z' tasks goes to the first
+// two warps).
 constexpr int kIssuer = kThreads - 32;
 // Staged tiles visible to the tensor cores; every thread past the previous chunk's
 // tensor-memory reads.

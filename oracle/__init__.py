@@ -41,6 +41,8 @@ class Params(ctypes.Structure):
         ("concealed_is_support", ctypes.c_int),
         ("store_f32", ctypes.c_int),
         ("quantize_inloop", ctypes.c_int),
+        ("perturb", ctypes.c_double),
+        ("perturb_seed", ctypes.c_uint64),
     ]
 
 
@@ -77,7 +79,7 @@ def params(profile: str = "efficient", **kw) -> Params:
     t_phi, t_nu = PROFILES[profile]
     p = Params(t_phi=t_phi, t_nu=t_nu, sigma2=10.0, ring_step=4, ridge_rel=1e-3,
                beta_kmin=-8, beta_kmax=16, beta_tie_rel=1e-3, concealed_is_support=1,
-               store_f32=0, quantize_inloop=0)
+               store_f32=0, quantize_inloop=0, perturb=0.0, perturb_seed=0)
     for k, v in kw.items():
         setattr(p, k, v)
     return p
@@ -114,9 +116,17 @@ def _load():
             ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_void_p,
             ctypes.POINTER(Stats), ctypes.c_int]
         assert lib.oracle_trace_rec_size() == ctypes.sizeof(TraceRec)
+        assert lib.oracle_params_size() == ctypes.sizeof(Params)
+        lib.oracle_splitmix64.restype = ctypes.c_uint64
+        lib.oracle_splitmix64.argtypes = [ctypes.c_uint64]
         assert lib.oracle_stats_size() == ctypes.sizeof(Stats)
         _lib = lib
     return _lib
+
+
+def splitmix64(x: int) -> int:
+    """The generator behind the ``perturb`` option (SplitMix64 output of state x)."""
+    return int(_load().oracle_splitmix64(ctypes.c_uint64(x & (2 ** 64 - 1))))
 
 
 def trace_to_numpy(buf) -> np.ndarray:

@@ -83,6 +83,13 @@ typedef struct {
     int quantize_inloop; /* R8 variant: every estimate is written back into the support
                             rounded to an 8-bit integer (round half to even), as a decoder
                             that keeps 8-bit frames does; the trace keeps the estimate */
+    double perturb;      /* sensitivity variant (test infrastructure, not the method): every
+                            written-back estimate is moved by perturb * u before the clip of
+                            R8, u in [-1, 1) drawn by SplitMix64 from (block, step, pixel,
+                            perturb_seed); 0 leaves the method unchanged.  It measures how
+                            far the sequential fill carries an error of a given size made
+                            at one step, the way a path with that per-step error would */
+    uint64_t perturb_seed;
 } oracle_params;
 
 typedef struct {
@@ -147,6 +154,19 @@ static int popcount_window(unsigned char A[OR_REG][OR_REG], int r0, int c0) {
 }
 
 static double clip255(double v) { return v < 0.0 ? 0.0 : (v > 255.0 ? 255.0 : v); }
+
+/* SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+   OOPSLA 2014): the output function applied to a counter; 53 bits mapped to [-1, 1) */
+uint64_t oracle_splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static double splitmix_unit(uint64_t x) {
+    return (double)(oracle_splitmix64(x) >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
 
 /* is frame pixel (fy, fx) lost: its block's flag, or its own flag under R9 */
 static int pixel_lost(const oracle_job* job, int fy, int fx) {
@@ -579,6 +599,11 @@ static void conceal_block(oracle_job* job, oracle_scratch* s, int by, int bx) {
            the patch only (they are the unavailable ones) */
         const int fr[4] = {pr, pr, pr + 1, pr + 1}, fc[4] = {pc, pc + 1, pc, pc + 1};
         for (int a = 0; a < 4; a++) {
+            if (p->perturb != 0.0) {
+                const uint64_t key = (((uint64_t)(by * job->mbw + bx) * 64u + (uint64_t)step) * 4u +
+                                      (uint64_t)a) ^ (p->perturb_seed * 0x100000001B3ull);
+                xhat[a] += p->perturb * splitmix_unit(key);
+            }
             xhat[a] = clip255(xhat[a]);
             if (p->store_f32) xhat[a] = (double)(float)xhat[a];
             if (s->A[fr[a]][fc[a]]) continue;
@@ -783,4 +808,5 @@ int oracle_conceal_px(const uint8_t* frame, int W, int H, int pitch, const uint8
 }
 
 int oracle_trace_rec_size(void) { return (int)sizeof(oracle_trace_rec); }
+int oracle_params_size(void) { return (int)sizeof(oracle_params); }
 int oracle_stats_size(void) { return (int)sizeof(oracle_stats); }

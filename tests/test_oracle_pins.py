@@ -577,3 +577,48 @@ def test_single_lost_pixel_hql_matches_numpy_brute_force(seed):
     assert abs(a_cf - t0["alpha"]) < 1e-9
     assert np.max(np.abs(np.clip(xhat, 0, 255) - t0["x"])) < 1e-8
     assert r["out"][50, 51] == t0["x"][1]
+
+
+# ------------------------------------------------------------------------------------
+# Sensitivity option (test infrastructure, not the method): a seeded perturbation of
+# every written-back estimate, used to measure how far the sequential fill carries a
+# per-step error of a given size.
+
+def test_splitmix64_matches_the_published_sequence():
+    # SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) seeded with 1234567: the first five
+    # outputs of the reference generator, whose state advances by 0x9E3779B97F4A7C15
+    expected = [6457827717110365317, 3203168211198807973, 9817491932198370423,
+                4593380528125082431, 16408922859458223821]
+    state = 1234567
+    for v in expected:
+        assert oracle.splitmix64(state) == v
+        state = (state + 0x9E3779B97F4A7C15) % 2 ** 64
+
+
+def test_perturb_zero_leaves_the_method_unchanged():
+    f = synth.make_frame(128, 96, 21, fine_texture=True)
+    m = synth.loss_runs(128, 96, 22, 0.3)
+    a = oracle.conceal(f, m, oracle.params("efficient"), trace=True)
+    b = oracle.conceal(f, m, oracle.params("efficient", perturb=0.0, perturb_seed=7), trace=True)
+    assert np.array_equal(a["out"], b["out"])
+    assert np.array_equal(a["trace"]["x"], b["trace"]["x"])
+
+
+def test_perturb_moves_each_write_by_at_most_delta_around_the_constant():
+    # constant frame: every estimate of every layer is the constant (the contexts hold only
+    # the constant and earlier writes), so with a perturbation each write is the mean of
+    # earlier values within the constant +- k*delta, moved by at most delta
+    c, delta = 100.0, 0.25
+    f = np.full((64, 64), int(c), np.uint8)
+    m = isolated(f, 1, 1)
+    r = oracle.conceal(f, m, oracle.params("efficient", perturb=delta, perturb_seed=3), trace=True)
+    x = r["trace"]["x"][0]                       # 64 steps x 4 pixels, in fill order
+    dev = np.abs(x - c)
+    assert dev.max() <= 64 * delta and dev.max() > 0
+    first = x[0] - c                             # first step: the context is all received
+    assert np.all(np.abs(first) <= delta) and np.any(first != 0)
+    # zero-mean draws: over 256 writes the mean deviation is far below delta
+    assert abs(float(np.mean(x - c))) < 0.25 * delta
+    # another seed draws other values
+    r2 = oracle.conceal(f, m, oracle.params("efficient", perturb=delta, perturb_seed=4), trace=True)
+    assert not np.array_equal(r2["trace"]["x"][0], x)

@@ -22,6 +22,33 @@ def test_ssim_identity_and_degradation():
     assert abs(bench.ssim(f, g) - bench.ssim(g, f)) < 1e-12
 
 
+def test_ssim_of_constant_images_is_the_luminance_term():
+    # SSIM (Wang, Bovik, Sheikh, Simoncelli 2004) with K1 = 0.01, K2 = 0.03, L = 255: on two
+    # constant images every local variance and covariance is 0, so each pixel's index is
+    # (2 a b + C1) / (a^2 + b^2 + C1), C1 = (0.01 * 255)^2 = 6.5025
+    a, b = 100.0, 120.0
+    fa = np.full((40, 56), a, np.uint8)
+    fb = np.full((40, 56), b, np.uint8)
+    c1 = 6.5025
+    expected = (2 * a * b + c1) / (a * a + b * b + c1)  # 24006.5025 / 24406.5025
+    assert abs(bench.ssim(fa, fb) - expected) < 1e-12
+    assert abs(expected - 0.983610925) < 1e-9  # 1 - 400 / 24406.5025
+
+
+def test_ssim_of_an_intensity_shift_keeps_contrast_and_structure():
+    # b = a + 30 (no clipping): local variances and the covariance are equal, so the
+    # contrast-structure factor (2 s_ab + C2) / (s_a^2 + s_b^2 + C2) is exactly 1 and the index
+    # is the luminance term of the two local means, mu_b = mu_a + 30
+    from scipy.ndimage import gaussian_filter
+    f = synth.make_frame(64, 48, 5).astype(np.float64)
+    f = np.clip(f, 0, 200)
+    g = f + 30.0
+    mu = gaussian_filter(f, 1.5)
+    c1 = 6.5025
+    lum = (2 * mu * (mu + 30.0) + c1) / (mu * mu + (mu + 30.0) ** 2 + c1)
+    assert abs(bench.ssim(f.astype(np.uint8), g.astype(np.uint8)) - float(lum.mean())) < 1e-9
+
+
 def test_clock_summary_reads_nvidia_smi_samples(tmp_path):
     # lines as `nvidia-smi --format=csv,noheader,nounits` writes them: index, SM clock, max
     # SM clock, power, active reasons mask, then the four reason columns

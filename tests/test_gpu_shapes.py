@@ -11,13 +11,11 @@ import pytest
 
 from paper_2205_11226_gb300 import skmmse, synth
 
-from parity import assembled_psnr_delta, compare, free_running_summary, run_forced, run_pair
+from parity import PSNR_TOL, assembled_psnr_delta, check_free, compare, run_forced
 
 pytestmark = pytest.mark.gpu
 
 TOL = {skmmse.FP32: 1e-3, skmmse.MIXED_FP16: 0.5}
-FREE_TOL = {skmmse.FP32: 0.25, skmmse.MIXED_FP16: 0.5}
-NEAR_TIE = {skmmse.FP32: 1.0, skmmse.MIXED_FP16: 10.0}
 
 
 def _check(f, px, p, ctx):
@@ -25,11 +23,10 @@ def _check(f, px, p, ctx):
     rep = compare(f, px, gpu, orc, p, forced=True, tol=TOL[p.precision])
     assert rep["compared"] + rep["flips"] == rep["patches"], rep
     assert rep["flips"] <= max(2, rep["patches"] // 200), rep
-    assert assembled_psnr_delta(f, px, gpu, orc) <= 0.01
-    g2, o2 = run_pair(f, px, p, ctx)
-    compare(f, px, g2, o2, p, tol=FREE_TOL[p.precision], near_tie=NEAR_TIE[p.precision])
-    s = free_running_summary(f, px, g2, o2)
-    assert abs(s["psnr_gpu"] - s["psnr_oracle"]) <= 0.1, s
+    assert assembled_psnr_delta(f, px, gpu, orc) <= PSNR_TOL
+    # free-running, within bounds derived from the oracle's own sensitivity to per-step
+    # errors of the size just measured
+    _, _, _, g2, _ = check_free(f, px, p, ctx, rep["max_err"])
     lost = px.astype(bool)
     assert np.array_equal(g2["out"][~lost], f[~lost])
     return rep

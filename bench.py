@@ -39,9 +39,7 @@ sys.path.insert(0, ROOT)
 METRIC = "concealed 16x16 MBs/s and 1080p frames/s on 1 GB300, mixed vs FP32, at \u22640.01 dB PSNR delta"
 UNIT = "MB/s"
 WORKLOAD = "batch64_mixed_24x352x288_24x1280x720_16x1920x1080_loss5-30pct"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+FP32_LANES_PER_SM = 128  # FP32 lanes of one sm_103a SM (4 partitions x 32)
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
 DTYPES = {"fp32": "f32", "bf16": "bf16+f32", "fp16": "f16+f32"}
 
@@ -58,8 +56,10 @@ def parse():
     ap.add_argument("--workload", choices=list(WORKLOADS) + ["serve", "sweep"], default="batch",
                     help="batch (the benchmark), a smaller case for profiling, the serving stream, "
                          "or the profile / T_nu sweep")
-    ap.add_argument("--serve-requests", type=int, default=2000,
-                    help="serving stream length (20000 = the full 600 frames/s stream of ~33 s)")
+    ap.add_argument("--serve-requests", type=int, default=20000,
+                    help="serving stream length (20000: the full 600 frames/s stream of ~33 s)")
+    ap.add_argument("--serve-oracle-every", type=int, default=50,
+                    help="serving: the oracle is timed on every n-th request (0: not at all)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the occupancy-maximal grid")
     ap.add_argument("--no-graph", action="store_true",
                     help="time direct skmmse_conceal_batch calls instead of the CUDA graph")
@@ -67,6 +67,11 @@ def parse():
                     help="bf16 / fp16: HQL contractions on tensor cores (mixed); fp32: CUDA cores only")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the FP32 / single-frame / 1080p comparison legs")
+    ap.add_argument("--no-phase", action="store_true", help="skip the per-phase roofline leg")
+    ap.add_argument("--phase-leg", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--ctas", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--tile-cov", type=int, default=64, help=argparse.SUPPRESS)
+    ap.add_argument("--tile-dist", type=int, default=64, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -212,6 +217,13 @@ def cpu_baseline(frames, masks, p_gpu, budget_s: float = 25.0):
     line = {"value": mbs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{len(outs)} frames of the batch (352x288, 1280x720, 1920x1080 at the "
                       f"batch's seeds), {mbs} lost blocks, {dt:.1f} s, all host cores"}
+    # one thread: the 352x288 frame of the sample
+    f, m = picked[0]
+    t1 = time.perf_counter()
+    oracle.conceal(f, m, p, threads=1)
+    dt1 = time.perf_counter() - t1
+    line["single_thread"] = {"value": int(m.sum()) / dt1, "unit": UNIT, "cores": 1,
+                             "sample": f"the 352x288 frame of the sample, {int(m.sum())} lost blocks, {dt1:.1f} s"}
     return line, [(f, m, o) for (f, m), o in zip(picked, outs)]
 
 
@@ -261,25 +273,22 @@ def measured_peaks_file():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def unit_rooflines(skmmse, st, n_lost, frames, mean_ms, precision, stream):
+def unit_rooflines(pk, st, n_lost, frames, mean_ms, precision):
     """Fractions of the other units for one step, from the kernel's own counts.
     - alu: the algorithmic FP32 operations against the FMA rate measured by the library's
       probe (skmmse_probe_peaks) on this GPU;
     - exp: exponentials of the method (one per IDL candidate evaluation, |G| per HQL
       candidate for the beta grid, |I0| per HQL candidate for the leave-one-out pass)
       against the probed exp2 rate;
-    - tensor: MMA operations issued by the HQL contractions (per 64-candidate chunk:
-      covariance 16 MMAs of 64x48x16, distances 6 of 64x32x16, beta sums 12 of 64x48x16)
-      against the measured dense BF16 rate (FP16 runs at the same rate);
+    - tensor: MMA operations issued by the HQL contractions, as the kernel counts them (per
+      64-candidate chunk: covariance 4 MMAs of 64x48x16, 16 when a staged value has a
+      fraction; distances 6 of 64x32x16; beta sums 8 of 64x48x16, 12 when a candidate value
+      has a fraction) against the measured dense BF16 rate (FP16 runs at the same rate);
     - hbm: frame bytes read and written per step against the measured copy bandwidth."""
-    pk = skmmse.probe_peaks(stream)
     peaks, src = measured_peaks_file()
     sec = mean_ms * 1e-3
     exps = st["idl_cand_evals"] + st["n_beta"] * st["hql_cands"] + st["hql_i0_cands"]
-    chunks = st["hql_cands"] / 64.0 + 0.5 * st["n_hql"]
-    mma = chunks * (16 * 2 * 64 * 48 * 16 + 6 * 2 * 64 * 32 * 16 + 12 * 2 * 64 * 48 * 16)
-    if precision == "fp32":
-        mma = 0.0
+    mma = float(st["mma_flops"])
     hbm_bytes = 2 * sum(f.size for f in frames) + n_lost * (256 * 4 * 2)
     out = {
         "alu_probe": {"achieved": st["alg_flops"] / sec / 1e12, "peak": pk["fma_tflops"], "unit": "TFLOP/s",
@@ -295,6 +304,87 @@ def unit_rooflines(skmmse, st, n_lost, frames, mean_ms, precision, stream):
                 "frac": hbm_bytes / sec / 1e9 / peaks["hbm_gbs"], "bytes_per_step": int(hbm_bytes),
                 "peak_source": f"copy bandwidth, {src}"},
     }
+    return out
+
+
+PHASES = ["stage", "ctx", "brl", "idl", "h_cand", "h_cov", "h_chol", "h_dist", "h_beta", "h_i0",
+          "h_alpha", "h_est", "writeback", "publish"]
+
+
+def run_phase_leg(args):
+    """(Subprocess, SKMMSE_PHASE_CLOCKS=1.)  One batch call of the phase-clock build at the
+    timed precision and persistent grid; prints the per-phase SM cycles and the counters."""
+    import torch
+    from paper_2205_11226_gb300 import build as skbuild
+    skbuild.build(phase=True)
+    from paper_2205_11226_gb300 import skmmse
+    torch.cuda.set_device(0)
+    frames, masks = build_workload(args.seed, args.workload)
+    p = skmmse.params(args.profile, precision=PRECISIONS[args.precision])
+    ctx = skmmse.Context()
+    ctx.set_config(args.ctas, args.tile_cov, args.tile_dist)
+    fd = [torch.from_numpy(f).cuda() for f in frames]
+    md = [torch.from_numpy(m).cuda() for m in masks]
+    ctx.conceal_batch(fd, md, p)
+    torch.cuda.synchronize()
+    _, st = ctx.conceal_batch(fd, md, p, stats=True)
+    ph = ctx.read_phase_clocks()
+    print(json.dumps({"phase": ph, "stats": st}), flush=True)
+    ctx.close()
+
+
+def phase_rooflines(args, cfg, sm_mhz, pk, n_sm):
+    """Per-phase fractions of the SM's measured FP32 and exp2 rates, each scaled to one CTA's
+    share of its SM (1 / CTAs per SM), from the phase-clock build run on the same batch.
+    A phase's cycles are thread 0's, summed over CTAs (barrier waits included); its
+    algorithmic work comes from the kernel's counters with the per-layer formulas of the
+    stats header (an exp counts as one operation)."""
+    env = dict(os.environ, SKMMSE_PHASE_CLOCKS="1")
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--phase-leg", "--precision", args.precision,
+           "--profile", args.profile, "--seed", str(args.seed), "--workload", args.workload,
+           "--ctas", str(cfg["ctas_per_sm"]), "--tile-cov", str(cfg["tile_cov"]),
+           "--tile-dist", str(cfg["tile_dist"])]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        return {"error": (r.stderr or r.stdout)[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    ph, st = d["phase"], d["stats"]
+    ctas_per_sm = cfg["ctas_per_sm"] or 2  # 0: the occupancy maximum
+    f_hz = sm_mhz * 1e6
+    fma_per_cyc = pk["fma_tflops"] * 1e12 / (n_sm * f_hz) / ctas_per_sm   # one CTA's share
+    ex2_per_cyc = pk["ex2_per_s"] / (n_sm * f_hz) / ctas_per_sm
+    nb = st["n_beta"]
+    m, mny, mny2 = st["hql_cands"], st["hql_ny_cands"], st["hql_ny2_cands"]
+    i0m, i0mny = st["hql_i0_cands"], st["hql_i0_ny_cands"]
+    work = {  # (FP32 operations, exps)
+        "ctx+brl": (3 * st["patch_ny"], 0),
+        "idl": (3 * st["idl_ny_evals"] + 11 * st["idl_cand_evals"], st["idl_cand_evals"]),
+        "h_cov": (mny2 + 11 * mny + 8 * m, 0),
+        "h_chol": (2 * st["hql_ny3"] // 3, 0),
+        "h_dist": (mny2 + 3 * mny, 0),
+        "h_beta": (nb * (2 * mny + 13 * m), nb * m),
+        "h_alpha": (5 * i0mny + 13 * i0m, i0m),
+    }
+    cyc = dict(ph)
+    cyc["ctx+brl"] = ph["ctx"] + ph["brl"]
+    total = sum(ph[k] for k in PHASES)
+    out = {"unit": "fraction of one CTA's share of the SM's probed rate", "ctas_per_sm": ctas_per_sm,
+           "sm_mhz": sm_mhz, "cycles_total": total, "phases": {}}
+    for k, (w, e) in work.items():
+        c = cyc[k]
+        if c <= 0:
+            continue
+        out["phases"][k] = {"share_of_cycles": c / total, "alg_ops": w, "exps": e,
+                            "alu_frac": w / (c * fma_per_cyc), "exp_frac": e / (c * ex2_per_cyc),
+                            "cycles_per_unit": c / max(1, {"ctx+brl": st["n_patches"], "idl": st["n_idl"] + st["n_hql"]}.get(k, st["n_hql"]))}
+    for k in ("stage", "h_cand", "h_i0", "h_est", "writeback", "publish"):
+        out["phases"][k] = {"share_of_cycles": ph[k] / total}
+    if st["mma_flops"]:
+        useful = 2 * (mny2 + 10 * mny + 25 * m) + 2 * mny2 + 2 * nb * (mny + 5 * m)
+        out["tensor"] = {"issued_flops": st["mma_flops"], "useful_flops": useful,
+                         "useful_over_issued": useful / st["mma_flops"],
+                         "note": "useful: Z'^T Z' over the Ny+5 live rows, E L^-T over Ny x Ny, W Z' over "
+                                 "|G| x (Ny+5), per HQL candidate"}
     return out
 
 
@@ -364,6 +454,8 @@ def compare_legs(ctx, skmmse, args, frames, masks, fd, md, od, p_main, ms_main, 
                                      f"{int(m1.sum())} lost blocks, one call per frame",
             # free-running: a near-tie decision that flips moves its whole dependency chain
             "psnr_delta_db_vs_fp32_max_frame": max(dframes),
+            "psnr_delta_db_vs_fp32_per_frame": [round(v, 4) for v in dframes],
+            "frames_differing_from_fp32": int(sum(1 for v in dframes if v > 0)),
             "psnr_delta_db_vs_fp32_median_frame": float(np.median(dframes)),
             "psnr_delta_db_vs_fp32_pooled": abs(pooled["main"] - pooled["fp32"]),
             "max_abs_diff_gray_vs_fp32_uint8": dmax}
@@ -394,7 +486,7 @@ def run_ours(args):
     any_px = any(m.shape == f.shape for f, m in zip(frames, masks))
 
     tuned = None
-    if not args.no_autotune:  # persistent CTAs per SM, picked by timing this batch
+    if not args.no_autotune:  # CTAs per SM and tensor-core tiles, picked by timing this batch
         tuned = ctx.autotune(fd, md, p, outs=od, reps=1, stream=stream)
     graph = None
     if not args.no_graph:     # the batch call (queue construction + persistent kernel) as a graph
@@ -470,12 +562,22 @@ def run_ours(args):
     flops = float(st["alg_flops"])
     mean_ms = total_ms / args.steps
     achieved = flops / (mean_ms * 1e-3) / 1e12
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    max_mhz = clocks["sm_max_mhz"] if clocks else None
+    if not max_mhz:  # no clock samples: the device's maximum SM clock as the driver reports it
+        max_mhz = query_max_sm_mhz(local)
+    peak = n_sm * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived)",
+                "peak_source": f"FP32 FMA: {n_sm} SMs (device) x {FP32_LANES_PER_SM} lanes x 2 FLOP x "
+                               f"{max_mhz:.0f} MHz (sampled maximum SM clock); derived",
                 "alg_flops_per_step": flops}
-    other_rooflines = unit_rooflines(skmmse, st, n_lost, frames, mean_ms, args.precision, stream)
+    pk = skmmse.probe_peaks(stream)
+    other_rooflines = unit_rooflines(pk, st, n_lost, frames, mean_ms, args.precision)
+    phase_line = None
+    if ws == 1 and not args.no_phase:
+        phase_line = phase_rooflines(args, ctx.get_config(fd, md, p), clocks["sm_mhz"] if clocks else max_mhz,
+                                     pk, n_sm)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -487,8 +589,8 @@ def run_ours(args):
             "config": {"workload": WORKLOADS[args.workload], "frames": len(frames), "lost_mbs_per_step": n_lost,
                        "profile": args.profile, "precision": args.precision,
                        "l2": "flushed between steps (256 MiB write)",
-                       "ctas_per_sm": tuned["ctas_per_sm"] if tuned else "occupancy max",
-                       "autotune_ms": tuned["ms"] if tuned else None,
+                       "launch_config": ctx.get_config(fd, md, p),
+                       "autotune_options": tuned["options"] if tuned else None,
                        "launch": "CUDA graph of the batch call" if graph is not None else "direct call",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -498,6 +600,7 @@ def run_ours(args):
             "gpu_launches": (5 if any_px else 4) * args.steps,
             "roofline": roofline,
             "rooflines_other": other_rooflines,
+            "rooflines_phase": phase_line,
             "layers": {k: st[k] for k in ("n_patches", "n_brl", "n_idl", "n_hql", "n_brl_nocand")},
             "wall_s_timed": t_wall,
             "clocks": clocks}
@@ -525,6 +628,16 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def query_max_sm_mhz(index: int) -> float:
+    """Maximum SM clock of the device (nvidia-smi query; 2070 MHz on GB300 if unavailable)."""
+    try:
+        r = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=clocks.max.sm",
+                            "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        return float(r.stdout.strip().splitlines()[0])
+    except Exception:
+        return 2070.0
+
+
 def synth_lost_mask(mask, shape):
     from paper_2205_11226_gb300 import synth
     if mask.shape == tuple(shape):
@@ -540,7 +653,8 @@ def oracle_agreement(ctx, skmmse, p, sample):
     outputs against the undamaged frame)."""
     from paper_2205_11226_gb300 import synth
     res = {"frames": len(sample), "blocks": 0, "flips": {}, "blocks_without_flip": 0,
-           "max_abs_err_gray_no_flip": 0.0, "psnr_delta_db_max": 0.0}
+           "max_abs_err_gray_no_flip": 0.0, "psnr_delta_db_max": 0.0, "psnr_delta_db_per_frame": [],
+           "max_abs_diff_gray_uint8": 0}
     for f, m, orc in sample:
         gpu = skmmse.conceal_numpy(f, m, p, trace=True, ctx=ctx)
         H, W = f.shape
@@ -581,8 +695,11 @@ def oracle_agreement(ctx, skmmse, p, sample):
             res["max_abs_err_gray_no_flip"] = max(res["max_abs_err_gray_no_flip"], e)
         lm = synth.lost_pixel_mask(m, W, H)
         ref = np.clip(np.rint(orc["out"]), 0, 255).astype(np.uint8)
-        res["psnr_delta_db_max"] = max(res["psnr_delta_db_max"],
-                                       abs(synth.psnr(gpu["out"], f, lm) - synth.psnr(ref, f, lm)))
+        dp = abs(synth.psnr(gpu["out"], f, lm) - synth.psnr(ref, f, lm))
+        res["psnr_delta_db_max"] = max(res["psnr_delta_db_max"], dp)
+        res["psnr_delta_db_per_frame"].append(round(dp, 4))
+        res["max_abs_diff_gray_uint8"] = max(res["max_abs_diff_gray_uint8"],
+                                             int(np.abs(gpu["out"].astype(np.int32) - ref.astype(np.int32))[lm].max()))
     return res
 
 
@@ -644,8 +761,9 @@ def forced_agreement(ctx, skmmse, p, frames_masks):
 
 def run_serve(args):
     """Serving stream (Poisson arrivals at 600 frames/s, sizes 1/3 each of 352x288,
-    1280x720, 1920x1080, loss U[2, 30] %): p50/p99 latency and sustained blocks/s, at
-    --precision and in FP32 on the same request stream."""
+    1280x720, 1920x1080, loss U[2, 30] %): p50/p99 latency, sustained blocks/s and the
+    device-measured concurrency of the launches, at --precision and in FP32 on the same
+    request stream; the FP64 oracle timed on every n-th request (host cores)."""
     import torch
     from paper_2205_11226_gb300 import build as skbuild
     skbuild.build()
@@ -657,7 +775,7 @@ def run_serve(args):
     for name in dict.fromkeys([args.precision, "fp32"]):
         p = skmmse.params(args.profile, precision=PRECISIONS[name])
         warm = serving.make_requests(64, seed=args.seed + 99, rate_hz=5000.0)
-        loop = serving.ServeLoop(p, n_streams=3)
+        loop = serving.ServeLoop(p, n_streams=2)
         loop.run(warm, realtime=True)
         loop.max_overlap = 0
         loop.n_batches = 0
@@ -669,16 +787,31 @@ def run_serve(args):
             clocks = clk.summary()
         loop.close()
     res = results[args.precision]
+    keys = ("mbs_per_s", "p50_ms", "p99_ms", "mean_ms", "batches", "max_overlap", "mean_resident_launches",
+            "max_resident_launches", "device_busy_s", "wall_s")
     line = {"metric": "served 16x16 MBs/s (Poisson 600 frames/s stream)", "value": res["mbs_per_s"],
             "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": DTYPES[args.precision],
             "data": "synthetic stream (seeded frames from a pool per size, per-request loss maps)",
             "config": {"workload": f"serve_{args.serve_requests}_requests_600hz", "profile": args.profile,
-                       "precision": args.precision, "streams": 3, "budget_bytes": 2 << 30},
-            "p50_ms": res["p50_ms"], "p99_ms": res["p99_ms"], "mean_ms": res["mean_ms"],
-            "requests": res["requests"], "batches": res["batches"], "max_overlap": res["max_overlap"],
-            "wall_s": res["wall_s"], "clocks": clocks,
-            "fp32": {k: results["fp32"][k] for k in ("mbs_per_s", "p50_ms", "p99_ms", "mean_ms", "batches",
-                                                      "max_overlap")}}
+                       "precision": args.precision, "streams": 2, "ctas_per_sm_per_stream": 1,
+                       "prealloc_device_bytes": res["prealloc_device_bytes"]},
+            "requests": res["requests"], "lost_mbs": res["lost_mbs"],
+            **{k: res[k] for k in keys}, "clocks": clocks,
+            "fp32": {k: results["fp32"][k] for k in keys}}
+    if args.serve_oracle_every > 0:  # the oracle on a seeded sample of the requests
+        import oracle
+        sample = reqs[::args.serve_oracle_every]
+        op = oracle_params_like(skmmse.params(args.profile))
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        mbs = 0
+        for r in sample:
+            oracle.conceal(r.frame, r.mb_lost, op, threads=cores)
+            mbs += r.n_lost
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": mbs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"every {args.serve_oracle_every}th request ({len(sample)} frames, "
+                                          f"{mbs} lost blocks, {dt:.0f} s); the stream's rate extrapolated"}
     print(json.dumps(line), flush=True)
 
 
@@ -750,7 +883,9 @@ def main():
     if args.workload == "sweep":
         run_sweep(args)
         return
-    if args.impl == "reference":
+    if args.phase_leg:
+        run_phase_leg(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

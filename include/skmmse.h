@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define SKMMSE_ABI_VERSION 2
+#define SKMMSE_ABI_VERSION 3
 
 typedef enum {
     SKMMSE_OK = 0,
@@ -169,8 +169,24 @@ typedef struct {
     long long hql_cands;        /* sum of M over HQL patches */
     long long hql_ny_cands;     /* sum of M*Ny over HQL patches */
     long long hql_i0_cands;     /* sum of |I0|*M over HQL patches */
-    long long alg_flops;        /* algorithmic FP32 operations of the call (per-layer formulas
-                                   of the design document; an exp counts as one) */
+    long long alg_flops;        /* algorithmic FP32 operations of the call, an exp counting as
+                                   one: per patch 3 Ny (context gather, flatness, mean); per IDL
+                                   candidate 3 Ny + 11 (distance, exp, five weighted sums); per
+                                   HQL patch with M candidates, Ny context values, |G| beta
+                                   values and |I0| = n0 members
+                                   M (Ny (Ny+1) + 8 Ny + 2 (Ny+4))     covariance C_YY, C_XY, sums
+                                   + M (Ny (Ny+1) + 2 Ny)              whitening and distance
+                                   + |G| M (2 (Ny+5) + 3)              beta grid
+                                   + n0 M (3 Ny + 2 (Ny+5) + 3)        leave-one-out */
+    long long hql_ny2_cands;    /* sum of M*Ny^2 over HQL patches */
+    long long hql_ny3;          /* sum of Ny^3 over HQL patches (the factorisation's order) */
+    long long hql_i0_ny_cands;  /* sum of |I0|*M*Ny over HQL patches */
+    long long patch_ny;         /* sum of Ny over all patches */
+    long long mma_flops;        /* tensor-core operations issued (2 M N K per tcgen05.mma), mixed
+                                   precision only */
+    long long t_first_inv_ns;   /* ~(start of the concealment kernel's first CTA), global timer */
+    long long t_last_ns;        /* end of its last CTA, global timer (ns): the launch's resident
+                                   interval is [~t_first_inv_ns, t_last_ns] */
     long long n_beta;           /* beta grid size of the call */
     int error;                  /* 0; else the device error word: 6 a wait gave up, 7 the
                                    work queue met an impossible chain height */
@@ -182,9 +198,9 @@ typedef struct skmmse_context skmmse_context;
 /* Library and ABI version (SKMMSE_ABI_VERSION). */
 int skmmse_abi_version(void);
 
-/* Size in bytes of skmmse_trace_rec / skmmse_stats / skmmse_params / skmmse_frame
-   (lets a binding check its struct layout). */
-int skmmse_struct_size(int which /* 0 trace, 1 stats, 2 params, 3 frame */);
+/* Size in bytes of skmmse_trace_rec / skmmse_stats / skmmse_params / skmmse_frame /
+   skmmse_config (lets a binding check its struct layout); -1 for other values. */
+int skmmse_struct_size(int which /* 0 trace, 1 stats, 2 params, 3 frame, 4 config */);
 
 /* Human-readable status. Never NULL. */
 const char* skmmse_status_str(skmmse_status s);
@@ -243,37 +259,77 @@ skmmse_status skmmse_graph_launch(skmmse_graph* g, void* stream);
 skmmse_status skmmse_graph_read_stats(skmmse_graph* g, skmmse_stats* h_stats, void* stream);
 void skmmse_graph_destroy(skmmse_graph* g);
 
-/* Autotuner of the persistent launch: conceals the given batch `reps` times (plus one
-   warm-up) for every number of CTAs per SM the kernel's occupancy allows (fewer CTAs give
-   each block more of the SM and shorten dependency chains; more CTAs run more blocks at
-   once), records the mean device time of each option in h_ms_per_option[k-1] (nullable,
-   8 entries) and keeps the fastest in the context (returned in *h_best, nullable).  The
-   outputs of the batch are written by every run.  Synchronous. */
+/* Launch configuration of the concealment kernel (the paper has no counterpart; none of these
+   changes a result: every block's arithmetic runs in one CTA in a fixed order, and the
+   tensor-core passes accumulate the same 16-candidate slices in the same order whatever
+   the tile):
+     ctas_per_sm  persistent CTAs per SM, 1 .. the occupancy maximum (2), 0 = the maximum;
+                  fewer CTAs give each block more of its SM and shorten dependency chains,
+                  more run more blocks at once;
+     tile_cov     candidates per chunk of the HQL covariance and beta-grid passes (the
+                  MMAs' K, Eqs. (8)-(10)): 32 or 64;
+     tile_dist    candidates per tile of the whitened-distance pass (the MMA's M, Eq. (6)
+                  with C_YY): 64 or 128.
+   The tiles apply to the mixed precisions; the FP32 path ignores them. */
+typedef struct {
+    int ctas_per_sm;
+    int tile_cov;
+    int tile_dist;
+} skmmse_config;
+#define SKMMSE_TUNE_MAX_OPTIONS 8
+
+/* Autotuner: conceals the given batch `reps` times (plus one warm-up) for every
+   configuration (CTAs per SM the occupancy allows x tile_cov {32, 64} x tile_dist {64, 128};
+   CTAs per SM only in FP32), and keeps the fastest for the batch's shape class in the
+   context: the calls and graphs of that class use it.  A shape class is the precision,
+   profile thresholds and support rule of p, and the number, sizes and mask kinds of the
+   frames (loss maps live in device memory and are not read).  Up to 64 classes are kept
+   (the oldest is replaced).  h_options / h_ms (nullable, SKMMSE_TUNE_MAX_OPTIONS entries)
+   receive the configurations timed and their mean device milliseconds, *h_n_options their
+   number and *h_best the index of the fastest (each nullable).  The outputs of the batch are
+   written by every run.  Synchronous. */
 skmmse_status skmmse_autotune(skmmse_context* ctx, const skmmse_frame* h_frames, int n,
                               const skmmse_params* p, int reps, void* stream,
-                              float* h_ms_per_option, int* h_best);
-/* Set the persistent CTAs per SM directly (0 = occupancy maximum). */
+                              skmmse_config* h_options, float* h_ms, int* h_n_options,
+                              int* h_best);
+/* The configuration used for shape classes the autotuner has not timed (initially
+   {0, 64, 64}).  Values outside the ranges above return SKMMSE_ERR_ARG. */
+skmmse_status skmmse_set_config(skmmse_context* ctx, const skmmse_config* cfg);
+/* The configuration a call with these frames and parameters would use. */
+skmmse_status skmmse_get_config(skmmse_context* ctx, const skmmse_frame* h_frames, int n,
+                                const skmmse_params* p, skmmse_config* out);
+/* Set the default's persistent CTAs per SM directly (0 = occupancy maximum). */
 skmmse_status skmmse_set_ctas_per_sm(skmmse_context* ctx, int ctas_per_sm);
 
 /* Largest frame, in 16x16 blocks (partial edge blocks included), that
    skmmse_conceal_noalloc accepts: 8192 covers 1920x1080 (120 x 68 = 8160 blocks). */
 #define SKMMSE_NOALLOC_MAX_MBS 8192
+/* Persistent CTAs skmmse_conceal_noalloc launches at most (each keeps the whitened vectors
+   of its current HQL step, 1849 x 32 floats, in the static scratch). */
+#define SKMMSE_NOALLOC_MAX_CTAS 128
+/* Bytes of the static device array behind skmmse_conceal_noalloc (about 39.1 MB). */
+#define SKMMSE_NOALLOC_SCRATCH_BYTES 39109888
 
 /* skmmse_conceal_noalloc: the same concealment as skmmse_conceal for one frame, for callers
    that cannot allocate device memory -- for example code running inside a memory pool or
    an allocator hook, under a strict device-memory budget, or anywhere a cudaMalloc would
    synchronise or fail.  The paper has no counterpart; this is an interface convenience.
    It calls no cudaMalloc, cudaFree, cudaMallocHost or allocating library routine.  Its
-   scratch (work queue, dependency flags, per-block values, counters) is one static device
-   array of about 8.6 MB, sized for SKMMSE_NOALLOC_MAX_MBS blocks; every GPU that loads the
-   library holds it until the process exits.  Larger frames return SKMMSE_ERR_TOO_LARGE.
-   The first call on a device looks up the array's device address and sets kernel
-   attributes for that device (make it before any stream capture on that device).  All
+   scratch (work queue, dependency flags, per-block values, counters, and the whitened
+   vectors of the HQL step each persistent CTA is on) is one static device array of
+   SKMMSE_NOALLOC_SCRATCH_BYTES (about 39.1 MB), sized for SKMMSE_NOALLOC_MAX_MBS blocks and
+   SKMMSE_NOALLOC_MAX_CTAS persistent CTAs; every GPU that loads the library holds it until
+   the process exits.  Larger frames return SKMMSE_ERR_TOO_LARGE.  The results are those of
+   skmmse_conceal (the number of persistent CTAs does not change them).
+   The first call on a device (and the first after the device's primary context was
+   replaced, e.g. by cudaDeviceReset) looks up the array's device address and sets kernel
+   attributes for that device: make it before any stream capture on that device.  All
    calls share the one array and it keeps the last call's contents: calls that may overlap
    on the GPU (different streams, or host threads without ordering) race; order them on one
    stream.  Arguments as skmmse_conceal (whole-block loss only); p->flags may hold
-   SKMMSE_FLAG_QUANTIZE only (no trace).  h_stats (nullable)
-   makes the call synchronous and returns the counters. */
+   SKMMSE_FLAG_QUANTIZE only (no trace).  h_stats (nullable) makes the call synchronous
+   and returns the counters.  Errors found on the device (a wait that gave up, status 6)
+   are reported only through h_stats: a call without h_stats cannot learn of them. */
 skmmse_status skmmse_conceal_noalloc(const uint8_t* d_frame, int width, int height, int pitch,
                                      const uint8_t* d_mb_lost, const skmmse_params* p,
                                      uint8_t* d_out, int out_pitch, float* d_out_f32,

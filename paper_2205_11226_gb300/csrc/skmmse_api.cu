@@ -21,6 +21,8 @@ using sk::KParams;
 using sk::WorkDev;
 
 static_assert(sizeof(sk::TraceRec) == sizeof(skmmse_trace_rec), "trace layout");
+// the counter slots map onto the leading long long fields of skmmse_stats, in order
+static_assert(offsetof(skmmse_stats, n_beta) == sizeof(long long) * sk::ST_COUNT, "stats layout");
 
 struct skmmse_context {
     int device = 0;
@@ -33,13 +35,16 @@ struct skmmse_context {
     // fixed device buffers
     int* d_counters = nullptr;               // [0] entries, [1] head, [2] error, [3] pad
     unsigned long long* d_stats = nullptr;   // kNStats
+    float* d_ubuf = nullptr;                 // kUbufFloats per persistent CTA (largest grid)
     // pinned staging for frame descriptors and tensor maps
     unsigned char* h_stage = nullptr;
     size_t h_stage_bytes = 0;
     cudaEvent_t stage_done = nullptr;
     bool stage_pending = false;
     long long last_nbeta = 0;
-    int ctas_per_sm = 0;  // persistent CTAs per SM (0: occupancy maximum; set by the autotuner)
+    skmmse_config dflt{0, 64, 64};  // configuration of shape classes not tuned
+    std::vector<std::pair<unsigned long long, skmmse_config>> tuned;  // per shape class
+    const skmmse_config* forced = nullptr;  // (the autotuner's option under test)
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
 };
 
@@ -109,9 +114,47 @@ KParams make_kparams(const skmmse_params* p) {
     k.flags = p->flags;
     k.mixed = p->precision;
     k.claim_idle_limit = (p->flags & SKMMSE_FLAG_SHORT_WAITS) ? 64u : (1u << 25);
+    k.tile_h13 = 64;
+    k.tile_h2 = 64;
     return k;
 }
 
+
+bool config_valid(const skmmse_config& c, int blocks_per_sm) {
+    return c.ctas_per_sm >= 0 && c.ctas_per_sm <= blocks_per_sm && (c.tile_cov == 32 || c.tile_cov == 64) &&
+           (c.tile_dist == 64 || c.tile_dist == 128);
+}
+
+// shape class of a call: precision, profile thresholds, support rule, and the number,
+// sizes and mask kinds of its frames (FNV-1a over those values)
+unsigned long long shape_key(const skmmse_frame* frames, int n, const skmmse_params* p) {
+    unsigned long long h = 1469598103934665603ull;
+    auto mix = [&](unsigned long long v) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (v >> (8 * i)) & 0xffu;
+            h *= 1099511628211ull;
+        }
+    };
+    unsigned tp, tn;
+    std::memcpy(&tp, &p->t_phi, 4);
+    std::memcpy(&tn, &p->t_nu, 4);
+    mix((unsigned long long)p->precision);
+    mix(((unsigned long long)tp << 32) | tn);
+    mix((unsigned long long)p->concealed_is_support);
+    mix((unsigned long long)n);
+    for (int i = 0; i < n; ++i)
+        mix(((unsigned long long)frames[i].width << 32) | ((unsigned long long)frames[i].height << 1) |
+            (frames[i].px_lost ? 1ull : 0ull));
+    return h;
+}
+
+skmmse_config resolve_config(const skmmse_context* c, const skmmse_frame* frames, int n, const skmmse_params* p) {
+    if (c->forced) return *c->forced;
+    const unsigned long long k = shape_key(frames, n, p);
+    for (const auto& e : c->tuned)
+        if (e.first == k) return e.second;
+    return c->dflt;
+}
 
 // ------------------------------------------------------------------------------------
 // kernel instantiations: FP32, and tensor-core contractions with BF16 or FP16 operands
@@ -225,7 +268,7 @@ void fill_descriptors(PFN_cuTensorMapEncodeTiled_v12000 encode, const skmmse_fra
 // outputs, counters cleared, queue built, persistent concealment kernel
 skmmse_status enqueue_batch(const skmmse_frame* frames, int n, const BatchLayout& L,
                             unsigned char* arena, int* counters, unsigned long long* stats,
-                            const KParams& kp, long long grid, cudaStream_t stream) {
+                            float* ubuf, const KParams& kp, long long grid, cudaStream_t stream) {
     for (int i = 0; i < n; ++i) {
         const skmmse_frame& f = frames[i];
         if (f.out != f.frame)
@@ -254,6 +297,7 @@ skmmse_status enqueue_batch(const skmmse_frame* frames, int n, const BatchLayout
     w.rem = reinterpret_cast<int*>(arena + L.o_rem);
     w.slots = reinterpret_cast<int*>(arena + L.o_slots);
     w.nbk = (int)L.max_mbs;
+    w.ubuf = ubuf;
     if (L.any_px) {  // block flags of the per-pixel masks, before the queue reads them
         sk::px_block_flags_kernel<<<n, sk::kThreads, 0, stream>>>(w, arena + L.o_mbmask);
         SK_CHECK(cudaGetLastError());
@@ -286,11 +330,13 @@ skmmse_status read_stats_from(const unsigned long long* d_stats, const int* d_co
 
 // ------------------------------------------------------------------------------------
 // Scratch for skmmse_conceal_noalloc(): one file-scope device array, sized for frames of up
-// to SKMMSE_NOALLOC_MAX_MBS blocks.  Every GPU that loads the library holds it until the
-// process exits.  Layout (byte offsets, each 256-aligned): frame descriptor, tensor map,
-// counters + stats, entry_of_mb, entries, done flags, per-block values, heights, buckets,
-// dependency counts, ready slots.
+// to SKMMSE_NOALLOC_MAX_MBS blocks and a persistent grid of at most SKMMSE_NOALLOC_MAX_CTAS
+// CTAs.  Every GPU that loads the library holds it until the process exits.  Layout (byte
+// offsets, each 256-aligned): frame descriptor, tensor map, counters + stats, entry_of_mb,
+// entries, done flags, per-block values, heights, buckets, dependency counts, ready slots,
+// the per-CTA whitened vectors of an HQL step.
 constexpr size_t kNaMax = SKMMSE_NOALLOC_MAX_MBS;
+constexpr size_t kNaCtas = SKMMSE_NOALLOC_MAX_CTAS;
 constexpr size_t kNaFrame = 0;
 constexpr size_t kNaTmap = 256;
 constexpr size_t kNaCounters = 512;
@@ -303,7 +349,9 @@ constexpr size_t kNaHgt = align_up(kNaVals + sizeof(float) * 256 * kNaMax, 256);
 constexpr size_t kNaBk = align_up(kNaHgt + sizeof(int) * kNaMax, 256);  // off, cnt, head, tail
 constexpr size_t kNaRem = align_up(kNaBk + sizeof(int) * 4 * kNaMax, 256);
 constexpr size_t kNaSlots = align_up(kNaRem + sizeof(int) * kNaMax, 256);
-constexpr size_t kNaBytes = align_up(kNaSlots + sizeof(int) * kNaMax, 256);
+constexpr size_t kNaUbuf = align_up(kNaSlots + sizeof(int) * kNaMax, 256);
+constexpr size_t kNaBytes = align_up(kNaUbuf + sizeof(float) * sk::kUbufFloats * kNaCtas, 256);
+static_assert(kNaBytes == SKMMSE_NOALLOC_SCRATCH_BYTES, "static scratch size stated in skmmse.h");
 static_assert(sizeof(FrameDev) <= 256 && sizeof(CUtensorMap) <= 256, "scratch header");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
@@ -327,6 +375,7 @@ __global__ void noalloc_setup_kernel(FrameDev fd, CUtensorMap tm, unsigned char*
 
 struct NoAllocDevice {
     bool ready = false;
+    unsigned long long ctx_id = 0;     // the primary context the set-up was made in
     unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch on this device
     int sm_count = 0;
     int blocks_per_sm = 0;
@@ -336,15 +385,45 @@ constexpr int kNaMaxDevices = 64;
 NoAllocDevice g_na_dev[kNaMaxDevices];
 std::mutex g_na_mu;
 
-// Once per device, with that device current: the device address of the scratch array
-// (the host-side symbol is only a stand-in), kernel attributes and occupancy.
+// Unique id of the current context (0 if none is current or the driver cannot tell).  A
+// device reset replaces the primary context and with it the scratch address and the kernel
+// attributes, so the set-up below is keyed on this id.
+unsigned long long current_context_id() {
+    using CtxCurrent = CUresult (*)(CUcontext*);
+    using CtxId = CUresult (*)(CUcontext, unsigned long long*);
+    static CtxCurrent get_current = nullptr;
+    static CtxId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxCurrent>(fn);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxId>(fn);
+        (void)cudaGetLastError();
+        looked_up = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Per device, with that device current, once per primary context: the device address of the
+// scratch array (the host-side symbol is only a stand-in), kernel attributes and occupancy.
 skmmse_status noalloc_setup(int dev, NoAllocDevice** out) {
     if (dev < 0 || dev >= kNaMaxDevices) return SKMMSE_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_na_mu);
     NoAllocDevice& d = g_na_dev[dev];
-    if (!d.ready) {
+    const unsigned long long id = current_context_id();
+    if (!d.ready || id == 0 || id != d.ctx_id) {
+        d.ready = false;
         void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);  // makes the primary context current
         if (e != cudaSuccess || ptr == nullptr) return cuda_fail(e);
         e = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = set_kernel_attributes();
@@ -360,6 +439,7 @@ skmmse_status noalloc_setup(int dev, NoAllocDevice** out) {
             d.encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
         (void)cudaGetLastError();
         d.scratch = static_cast<unsigned char*>(ptr);
+        d.ctx_id = current_context_id();
         d.ready = true;
     }
     *out = &d;
@@ -378,6 +458,7 @@ int skmmse_struct_size(int which) {
         case 1: return (int)sizeof(skmmse_stats);
         case 2: return (int)sizeof(skmmse_params);
         case 3: return (int)sizeof(skmmse_frame);
+        case 4: return (int)sizeof(skmmse_config);
         default: return -1;
     }
 }
@@ -428,6 +509,8 @@ skmmse_status skmmse_create(skmmse_context** out) {
                                                           sk::kThreads, c->smem_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_stats, sk::kNStats * sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&c->d_ubuf, sizeof(float) * sk::kUbufFloats * (size_t)c->sm_count * c->blocks_per_sm);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming);
     if (e == cudaSuccess) {
         void* fn = nullptr;
@@ -452,6 +535,7 @@ void skmmse_destroy(skmmse_context* c) {
     if (c->d_arena) cudaFree(c->d_arena);
     if (c->d_counters) cudaFree(c->d_counters);
     if (c->d_stats) cudaFree(c->d_stats);
+    if (c->d_ubuf) cudaFree(c->d_ubuf);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->stage_done) cudaEventDestroy(c->stage_done);
     delete c;
@@ -490,10 +574,13 @@ skmmse_status skmmse_conceal_batch(skmmse_context* c, const skmmse_frame* frames
     SK_CHECK(cudaMemcpyAsync(c->d_arena, c->h_stage, L.stage_bytes, cudaMemcpyHostToDevice, stream));
     SK_CHECK(cudaEventRecord(c->stage_done, stream));
     c->stage_pending = true;
-    const KParams kp = make_kparams(p);
+    KParams kp = make_kparams(p);
+    const skmmse_config cfg = resolve_config(c, frames, n, p);
+    kp.tile_h13 = cfg.tile_cov;
+    kp.tile_h2 = cfg.tile_dist;
     c->last_nbeta = kp.nbeta;
-    const long long grid = (long long)c->sm_count * (c->ctas_per_sm > 0 ? c->ctas_per_sm : c->blocks_per_sm);
-    s = enqueue_batch(frames, n, L, c->d_arena, c->d_counters, c->d_stats, kp, grid, stream);
+    const long long grid = (long long)c->sm_count * (cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : c->blocks_per_sm);
+    s = enqueue_batch(frames, n, L, c->d_arena, c->d_counters, c->d_stats, c->d_ubuf, kp, grid, stream);
     if (s != SKMMSE_OK) return s;
     if (h_stats) return skmmse_read_stats(c, h_stats, stream_v);
     return SKMMSE_OK;
@@ -506,6 +593,7 @@ struct skmmse_graph {
     unsigned char* d_arena = nullptr;
     int* d_counters = nullptr;
     unsigned long long* d_stats = nullptr;
+    float* d_ubuf = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long nbeta = 0;
@@ -518,6 +606,7 @@ void skmmse_graph_destroy(skmmse_graph* g) {
     if (g->d_arena) cudaFree(g->d_arena);
     if (g->d_counters) cudaFree(g->d_counters);
     if (g->d_stats) cudaFree(g->d_stats);
+    if (g->d_ubuf) cudaFree(g->d_ubuf);
     delete g;
 }
 
@@ -531,19 +620,23 @@ skmmse_status skmmse_graph_create(skmmse_context* c, const skmmse_frame* frames,
     skmmse_graph* g = new (std::nothrow) skmmse_graph();
     if (!g) return SKMMSE_ERR_NOMEM;
     std::vector<unsigned char> host(L.stage_bytes);
-    const KParams kp = make_kparams(p);
+    KParams kp = make_kparams(p);
+    const skmmse_config cfg = resolve_config(c, frames, n, p);
+    kp.tile_h13 = cfg.tile_cov;
+    kp.tile_h2 = cfg.tile_dist;
     g->nbeta = kp.nbeta;
-    const long long grid = (long long)c->sm_count * (c->ctas_per_sm > 0 ? c->ctas_per_sm : c->blocks_per_sm);
+    const long long grid = (long long)c->sm_count * (cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : c->blocks_per_sm);
     cudaStream_t cs = nullptr;
     cudaError_t e = cudaMalloc(&g->d_arena, L.need);
     if (e == cudaSuccess) fill_descriptors(c->encode, frames, n, p, L, host.data(), g->d_arena);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_counters, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_stats, sk::kNStats * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_ubuf, sizeof(float) * sk::kUbufFloats * (size_t)grid);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_arena, host.data(), L.stage_bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        s = enqueue_batch(frames, n, L, g->d_arena, g->d_counters, g->d_stats, kp, grid, cs);
+        s = enqueue_batch(frames, n, L, g->d_arena, g->d_counters, g->d_stats, g->d_ubuf, kp, grid, cs);
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         g->graph = graph;
@@ -576,22 +669,32 @@ skmmse_status skmmse_graph_read_stats(skmmse_graph* g, skmmse_stats* h, void* st
 }
 
 // ------------------------------------------------------------------------------------
-// autotuner: the persistent grid size
+// autotuner: persistent CTAs per SM and the tensor-core tile sizes, per shape class
 
 skmmse_status skmmse_autotune(skmmse_context* c, const skmmse_frame* frames, int n,
-                              const skmmse_params* p, int reps, void* stream_v,
-                              float* h_ms_per_option, int* h_best) {
-    if (!c || !frames || n < 1 || reps < 1) return SKMMSE_ERR_ARG;
+                              const skmmse_params* p, int reps, void* stream_v, skmmse_config* h_options,
+                              float* h_ms, int* h_n_options, int* h_best) {
+    if (!c || !frames || n < 1 || reps < 1 || !p) return SKMMSE_ERR_ARG;
+    std::vector<skmmse_config> opts;
+    const bool mixed = p->precision != SKMMSE_FP32;
+    for (int k = 1; k <= c->blocks_per_sm; ++k)
+        for (int tc_ : {64, 32})
+            for (int td : {64, 128}) {
+                if (!mixed && (tc_ != 64 || td != 64)) continue;
+                if ((int)opts.size() < SKMMSE_TUNE_MAX_OPTIONS) opts.push_back(skmmse_config{k, tc_, td});
+            }
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     cudaEvent_t a = nullptr, b = nullptr;
     SK_CHECK(cudaEventCreate(&a));
-    SK_CHECK(cudaEventCreate(&b));
-    const int saved = c->ctas_per_sm;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return SKMMSE_ERR_CUDA;
+    }
     float best = 1e30f;
-    int best_k = c->blocks_per_sm;
+    int best_i = 0;
     skmmse_status s = SKMMSE_OK;
-    for (int k = 1; k <= c->blocks_per_sm && s == SKMMSE_OK; ++k) {
-        c->ctas_per_sm = k;
+    for (int i = 0; i < (int)opts.size() && s == SKMMSE_OK; ++i) {
+        c->forced = &opts[i];
         s = skmmse_conceal_batch(c, frames, n, p, nullptr, stream_v);  // warm-up
         float tot = 0.0f;
         for (int r = 0; r < reps && s == SKMMSE_OK; ++r) {
@@ -604,22 +707,49 @@ skmmse_status skmmse_autotune(skmmse_context* c, const skmmse_frame* frames, int
             tot += ms;
         }
         const float avg = tot / reps;
-        if (h_ms_per_option && k <= 8) h_ms_per_option[k - 1] = avg;
+        if (h_options) h_options[i] = opts[i];
+        if (h_ms) h_ms[i] = avg;
         if (avg < best) {
             best = avg;
-            best_k = k;
+            best_i = i;
         }
     }
+    c->forced = nullptr;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    c->ctas_per_sm = (s == SKMMSE_OK) ? best_k : saved;
-    if (h_best) *h_best = c->ctas_per_sm;
-    return s;
+    if (s != SKMMSE_OK) return s;
+    const unsigned long long key = shape_key(frames, n, p);
+    bool found = false;
+    for (auto& e : c->tuned)
+        if (e.first == key) {
+            e.second = opts[best_i];
+            found = true;
+        }
+    if (!found) {
+        if (c->tuned.size() >= 64) c->tuned.erase(c->tuned.begin());
+        c->tuned.emplace_back(key, opts[best_i]);
+    }
+    if (h_n_options) *h_n_options = (int)opts.size();
+    if (h_best) *h_best = best_i;
+    return SKMMSE_OK;
+}
+
+skmmse_status skmmse_set_config(skmmse_context* c, const skmmse_config* cfg) {
+    if (!c || !cfg || !config_valid(*cfg, c->blocks_per_sm)) return SKMMSE_ERR_ARG;
+    c->dflt = *cfg;
+    return SKMMSE_OK;
+}
+
+skmmse_status skmmse_get_config(skmmse_context* c, const skmmse_frame* frames, int n, const skmmse_params* p,
+                                skmmse_config* out) {
+    if (!c || !frames || n < 1 || !p || !out) return SKMMSE_ERR_ARG;
+    *out = resolve_config(c, frames, n, p);
+    return SKMMSE_OK;
 }
 
 skmmse_status skmmse_set_ctas_per_sm(skmmse_context* c, int k) {
     if (!c || k < 0 || k > c->blocks_per_sm) return SKMMSE_ERR_ARG;
-    c->ctas_per_sm = k;
+    c->dflt.ctas_per_sm = k;
     return SKMMSE_OK;
 }
 
@@ -746,12 +876,14 @@ skmmse_status skmmse_conceal_noalloc(const uint8_t* d_frame, int width, int heig
     w.rem = reinterpret_cast<int*>(sc + kNaRem);
     w.slots = reinterpret_cast<int*>(sc + kNaSlots);
     w.nbk = (int)(mbw * mbh);
+    w.ubuf = reinterpret_cast<float*>(sc + kNaUbuf);
     const KParams kp = make_kparams(p);
     sk::queue_heights_kernel<<<1, sk::kThreads, 0, stream>>>(w, kp.concealed_is_support);
     sk::queue_offsets_kernel<<<1, sk::kThreads, 0, stream>>>(w);
     sk::queue_fill_kernel<<<1, sk::kThreads, 0, stream>>>(w, kp.concealed_is_support);
     SK_CHECK(cudaGetLastError());
     long long grid = (long long)nd->sm_count * nd->blocks_per_sm;
+    if (grid > (long long)kNaCtas) grid = (long long)kNaCtas;  // CTAs the static scratch serves
     if (grid > mbw * mbh) grid = mbw * mbh;
     if (grid < 1) grid = 1;
     launch_conceal(kp, w, (unsigned)grid, stream);

@@ -45,17 +45,26 @@ constexpr int kZrow = 44;        // row stride of the staged rows (a lane per ro
 constexpr int kMaxBeta = 32;
 constexpr int kMaxI0 = 33;
 constexpr int kNStats = 64;
-constexpr int kPhaseBase = 32;  // stats slots 32..47: phase clocks (SKMMSE_PHASE_CLOCKS builds)
+constexpr int kPhaseBase = 48;  // stats slots 48..63: phase clocks (SKMMSE_PHASE_CLOCKS builds)
 constexpr int kNPhase = 16;
+// whitened context differences u_j = L^-1 (y_j - y0) of one HQL step, kept in global
+// memory (per persistent CTA) from the distance pass for the leave-one-out pass: row j of
+// 32 floats, its float4 number c4 at float offset ubuf_pos(j, c4) (XOR-swizzled, the
+// order of the shared staging rows that feed the bulk copies)
+constexpr int kUbufFloats = kNcand * kMaxNy;
+__host__ __device__ __forceinline__ int ubuf_pos(int j, int c4) { return 4 * (c4 ^ (j & 7)); }
 
 // stats slots (match skmmse_stats field order)
 enum {
     ST_LOST = 0, ST_PATCH, ST_EMPTY, ST_BRL, ST_IDL, ST_HQL, ST_NOCAND,
     ST_RING0,  // 16 slots
     ST_IDL_EVALS = ST_RING0 + 16, ST_IDL_NY, ST_HQL_M, ST_HQL_MNY, ST_HQL_I0M, ST_FLOPS,
+    ST_HQL_MNY2, ST_HQL_NY3, ST_HQL_I0MNY, ST_PATCH_NY, ST_MMA_FLOPS,
+    ST_T_FIRST_INV,  // max over CTAs of ~(start time): the first CTA's start, complemented
+    ST_T_LAST,       // max over CTAs of the end time (global timer, ns)
     ST_COUNT
 };
-static_assert(ST_COUNT <= kNStats, "stats slots");
+static_assert(ST_COUNT <= kPhaseBase, "stats slots");
 
 enum { L_EMPTY = 0, L_BRL = 1, L_IDL = 2, L_HQL = 3, L_NOCAND = 4 };
 
@@ -95,6 +104,8 @@ struct KParams {
     unsigned flags;
     int mixed;            // 0: FP32 on the CUDA cores; 1: BF16, 2: FP16 tensor-core contractions
     unsigned claim_idle_limit;  // polls without progress before a CTA gives up claiming
+    int tile_h13;         // candidates per chunk of the covariance and beta passes: 32 or 64
+    int tile_h2;          // candidates per tile of the distance pass: 64 or 128 (MMA M)
 };
 
 struct FrameDev {
@@ -130,6 +141,7 @@ struct WorkDev {
     int* rem;                 // per entry: dependencies not yet done
     int* slots;               // per entry position: the ready entries of each bucket, -1 until published
     int nbk;                  // buckets allocated (>= blocks of the largest frame)
+    float* ubuf;              // per persistent CTA (blockIdx.x): kUbufFloats, u_j of the HQL step
 };
 
 struct TraceRec {             // layout of skmmse_trace_rec
@@ -195,7 +207,10 @@ struct __align__(16) Hql {
                 HqlP2 p2;
             };
         };
-        __align__(16) uint16_t mx[32768];  // tensor-core operand tiles (64 KB; layout in tl::)
+        // tensor-core operand tiles (64 KB; layout in tl::).  128-byte aligned in shared memory:
+        // a core matrix (8 rows of 16 bytes) then fills one 128-byte line, which the tensor
+        // core reads in one pass (at a 64-byte offset the passes measured ~1.6x slower)
+        __align__(128) uint16_t mx[32768];
         struct {  // leave-one-out pass: per-warp candidate buffers and the warps' partial sums
             __align__(16) float Wb[kWarps][32][kWb];
             float Mg[kWarps][33][10];
@@ -233,6 +248,7 @@ struct __align__(128) Smem {
         IdlSlot idl[2][kWarps];
         Hql hql;
     };
+    uint8_t order[64];                 // fill order of the block (patch of each step)
 };
 
 // ------------------------------------------------------------------------------------
@@ -307,6 +323,28 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map,
 
 __device__ __forceinline__ void tmap_acquire(const CUtensorMap* map) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
+// bulk copy shared -> global (async proxy), completion by bulk groups
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+                 "r"(smem_u32(ssrc)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() {  // sources read: staging reusable
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {  // writes performed, then visible to loads
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// the GPU's global timer (nanoseconds), comparable across the CTAs and launches of a device
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -422,28 +460,6 @@ constexpr float kNegBig = -1.0e30f;
 // ------------------------------------------------------------------------------------
 // IDL: Eq. (15) over growing rings; returns 1 accepted, 0 not accepted, -1 no candidate
 
-// next patch (R2): the unfilled patch with the most available pixels in its 6x6 window,
-// ties to the lowest index.  Warp-level: every lane returns the same patch.
-__device__ __forceinline__ int select_patch(const Smem& sm, int lane) {
-    const unsigned long long uf = sm.unfilled;
-    int best = -1;
-#pragma unroll
-    for (int h2 = 0; h2 < 2; ++h2) {
-        const int p = lane + 32 * h2;
-        if ((uf >> p) & 1ull) {
-            const int a = p >> 3, b = p & 7;
-            const int wr = kMB + 2 * a - 2, wc = kMB + 2 * b - 2;
-            int cnt = 0;  // the 6x6 window less the patch's own four pixels
-#pragma unroll
-            for (int r = 0; r < 6; ++r)
-                cnt += __popc((unsigned)(sm.av[wr + r] >> wc) & ((r == 2 || r == 3) ? 0x33u : 63u));
-            best = max(best, cnt * 64 + (63 - p));
-        }
-    }
-    best = __reduce_max_sync(0xffffffffu, best);
-    return 63 - (best & 63);
-}
-
 struct CtxStats {
     int ny;
     float phi, mean;  // flatness (max - min) and mean of the context, Eqs. (16)-(17)
@@ -489,6 +505,54 @@ __device__ __forceinline__ CtxStats ctx_stats(const Smem& sm, int wr, int wc, in
 // compiler keeps every access in the shared address space.
 extern __shared__ __align__(128) unsigned char smem_raw[];
 __device__ __forceinline__ Smem& smem_ref() { return *reinterpret_cast<Smem*>(smem_raw); }
+
+// Fill order of a block (R2: the unfilled patch with the most available pixels in its 6x6
+// window less the patch itself, ties to the lowest index).  It depends on availability only,
+// so warp 0 simulates it once when the block is staged.  Lane l holds patches l and l + 32
+// and their counts.  Filling patch p makes its unavailable pixels available; those lie in
+// the windows of exactly the 8 neighbouring patches (the window of q spans patch rows and
+// columns q +- 1), whose counts grow by that number.  order[s] = the patch of step s.
+__device__ __noinline__ void fill_order(int npatch) {
+    Smem& sm = smem_ref();
+    const int lane = threadIdx.x & 31;
+    const unsigned long long uf0 = sm.unfilled;
+    int cnt[2], newpx[2];
+    bool uf[2];
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+        const int p = lane + 32 * h2;
+        const int a = p >> 3, b = p & 7;
+        const int wr = kMB + 2 * a - 2, wc = kMB + 2 * b - 2;
+        int c = 0;
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+            c += __popc((unsigned)(sm.av[wr + r] >> wc) & ((r == 2 || r == 3) ? 0x33u : 63u));
+        cnt[h2] = c;
+        newpx[h2] = 4 - __popc((unsigned)(sm.av[wr + 2] >> (wc + 2)) & 3u) -
+                    __popc((unsigned)(sm.av[wr + 3] >> (wc + 2)) & 3u);
+        uf[h2] = ((uf0 >> p) & 1ull) != 0ull;
+    }
+    for (int s = 0; s < npatch; ++s) {
+        int key = -1;
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2)
+            if (uf[h2]) key = max(key, cnt[h2] * 64 + (63 - (lane + 32 * h2)));
+        const int best = __reduce_max_sync(0xffffffffu, key);
+        const int ps = 63 - (best & 63);
+        const int np = __shfl_sync(0xffffffffu, (ps >> 5) ? newpx[1] : newpx[0], ps & 31);
+        if (lane == 0) sm.order[s] = (uint8_t)ps;
+        const int as = ps >> 3, bs = ps & 7;
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int p = lane + 32 * h2;
+            const int da = (p >> 3) - as, db = (p & 7) - bs;
+            if (p == ps) uf[h2] = false;
+            else if (da >= -1 && da <= 1 && db >= -1 && db <= 1) cnt[h2] += np;
+        }
+    }
+    __syncwarp();
+}
+
 
 // Not inlined, with scalar arguments: the 36 context values live in registers only while
 // this function runs, so the per-step loop of the kernel keeps a small register footprint.
@@ -762,7 +826,7 @@ __device__ __forceinline__ void split2_cvt(float v0, float v1, uint32_t& hi2, ui
 // core matrix in each of the hi and lo tiles.  CVT: split through the conversion unit (the
 // whitening pass, H2, measured faster that way; the other passes measured faster without).
 template <bool BF16, bool CVT = false>
-__device__ __forceinline__ void store8_split(uint16_t* thi, uint16_t* tlo, int r, int k0, int K,
+__device__ __forceinline__ bool store8_split(uint16_t* thi, uint16_t* tlo, int r, int k0, int K,
                                              const float v[8]) {
     uint32_t h[4], l[4];
 #pragma unroll
@@ -773,12 +837,13 @@ __device__ __forceinline__ void store8_split(uint16_t* thi, uint16_t* tlo, int r
     const uint32_t off = tc::kmajor_offset(r, k0, K) >> 1;  // in 16-bit elements
     *reinterpret_cast<uint4*>(thi + off) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4*>(tlo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    return ((l[0] | l[1] | l[2] | l[3]) & 0x7FFF7FFFu) != 0u;  // a low half other than +-0
 }
 
 // 8 consecutive K values of row r, split into the integer part n = rint(v) (exact in both
 // 16-bit formats for |n| <= 256) and the fraction f = v - n as a high and a low 16-bit half
 template <bool BF16>
-__device__ __forceinline__ void store8_int_frac(uint16_t* tn, uint16_t* tfh, uint16_t* tfl, int r,
+__device__ __forceinline__ bool store8_int_frac(uint16_t* tn, uint16_t* tfh, uint16_t* tfl, int r,
                                                 int k0, int K, const float v[8]) {
     uint32_t n[4], fh[4], fl[4];
     constexpr float kRnd = 12582912.0f;  // 1.5 * 2^23: x + kRnd - kRnd rounds to an integer (RN)
@@ -793,6 +858,7 @@ __device__ __forceinline__ void store8_int_frac(uint16_t* tn, uint16_t* tfh, uin
     *reinterpret_cast<uint4*>(tn + off) = make_uint4(n[0], n[1], n[2], n[3]);
     *reinterpret_cast<uint4*>(tfh + off) = make_uint4(fh[0], fh[1], fh[2], fh[3]);
     *reinterpret_cast<uint4*>(tfl + off) = make_uint4(fl[0], fl[1], fl[2], fl[3]);
+    return ((fh[0] | fh[1] | fh[2] | fh[3] | fl[0] | fl[1] | fl[2] | fl[3]) & 0x7FFF7FFFu) != 0u;
 }
 
 // Operand tiles of the tensor-core passes in the 64 KB region h.mx (byte offsets), two
@@ -812,14 +878,11 @@ constexpr uint32_t kWinK32 = 64 * 32 * 2;  // M = 64, K = 32
 // in row 36); then the int32 sums
 constexpr uint32_t kH1Tile = 48 * 64 * 2, kH1Buf = 3 * kH1Tile, kH1Sums = 49152;
 constexpr uint32_t kH1SumsBytes = 36 * 40 * 4;
-// H2, K = 32: A = candidates (64 rows) high / low; B = L^-1 (32 rows) high / low
-constexpr uint32_t kH2A = 4096, kH2ABuf = 2 * kH2A, kH2B = 16384, kH2BTile = 2048;
+// H2: see H2L below (its layout depends on the candidates per tile)
 // H3, K = 64: A = weights (32 rows: beta) high / low; B = Z' (48 rows) high / low
 constexpr uint32_t kH3W = 4096, kH3WBuf = 2 * kH3W, kH3Z = 16384, kH3ZTile = 6144, kH3ZBuf = 2 * kH3ZTile;
 static_assert(kH1Buf + 2 * kH1Tile + kWinK64 <= kRegion && 2 * kH1Buf <= kH1Sums &&
                   kH1Sums + kH1SumsBytes <= kRegion, "H1 tiles");
-static_assert(kH2ABuf + kH2A + kWinK32 <= kRegion && 2 * kH2ABuf <= kH2B && kH2B + 2 * kH2BTile <= kRegion,
-              "H2 tiles");
 static_assert(kH3WBuf + kH3W + kWinK64 <= kRegion && 2 * kH3WBuf <= kH3Z && kH3Z + 2 * kH3ZBuf <= kRegion,
               "H3 tiles");
 }  // namespace tl
@@ -831,10 +894,12 @@ __device__ __forceinline__ void zero_region(Hql& h, uint32_t off, uint32_t bytes
     for (int i = threadIdx.x; i < (int)(bytes / 16); i += kThreads) p[i] = make_uint4(0, 0, 0, 0);
 }
 
-// D (+)= A * B^T over K columns with split operands (issued by one thread)
+// D (+)= A * B^T over K columns with split operands (issued by one thread).  b_lo_zero: every
+// low half of B is zero (B held exactly by its high halves), so the A-high x B-low product
+// is left out.
 __device__ __forceinline__ void mma3(uint32_t tmem, const uint16_t* ahi, const uint16_t* alo,
                                      const uint16_t* bhi, const uint16_t* blo, int K, uint32_t idesc,
-                                     bool accumulate) {
+                                     bool accumulate, bool b_lo_zero = false) {
     const uint32_t sbo = (uint32_t)(K / 8) * 128u;
     const uint32_t a0 = tc::smem_addr(ahi), a1 = tc::smem_addr(alo);
     const uint32_t b0 = tc::smem_addr(bhi), b1 = tc::smem_addr(blo);
@@ -842,7 +907,8 @@ __device__ __forceinline__ void mma3(uint32_t tmem, const uint16_t* ahi, const u
         const uint32_t o = (uint32_t)kk * 256u;
         tc::mma_f16(tmem, tc::smem_desc(a0 + o, 128, sbo), tc::smem_desc(b0 + o, 128, sbo), idesc,
                     accumulate || kk > 0);
-        tc::mma_f16(tmem, tc::smem_desc(a0 + o, 128, sbo), tc::smem_desc(b1 + o, 128, sbo), idesc, true);
+        if (!b_lo_zero)
+            tc::mma_f16(tmem, tc::smem_desc(a0 + o, 128, sbo), tc::smem_desc(b1 + o, 128, sbo), idesc, true);
         tc::mma_f16(tmem, tc::smem_desc(a1 + o, 128, sbo), tc::smem_desc(b0 + o, 128, sbo), idesc, true);
     }
 }
@@ -862,6 +928,15 @@ __device__ __forceinline__ void tiles_ready() {
     tc::fence_after();
 }
 
+// the same, returning whether any thread's flag is set (a CTA-uniform value)
+__device__ __forceinline__ bool tiles_ready_or(bool flag) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc::fence_before();
+    const bool any = __syncthreads_or(flag ? 1 : 0) != 0;
+    tc::fence_after();
+    return any;
+}
+
 template <typename IssueF>
 __device__ __forceinline__ void mma_issue(Smem& sm, IssueF issue) {
     if (threadIdx.x == kIssuer) {
@@ -878,8 +953,10 @@ __device__ __forceinline__ void mma_wait(Smem& sm, uint32_t& mph) {
 
 // stage rows 0..36 of Z^T for candidates [c0, c0+n): z' (feature rows 0..35, zero beyond
 // nz) and the constant one (row 36)
-template <bool BF16, bool INTFRAC>
-__device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, int nz, float shift, uint16_t* t0,
+// Returns whether this thread staged a value that one 16-bit part does not hold exactly (a
+// non-zero fraction, INTFRAC; a non-zero low half, otherwise).
+template <bool BF16, bool INTFRAC, int CH>
+__device__ __forceinline__ bool stage_zt(Smem& sm, int c0, int n, int nz, float shift, uint16_t* t0,
                                          uint16_t* t1, uint16_t* t2) {
     Hql& h = sm.hql;
     // live rows: the nz = 4 + Ny features and the constant (row 36); the other rows stay
@@ -890,12 +967,14 @@ __device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, int nz, float 
     // of each 8-lane group in reverse order: the live ones (rows 32..36) then fall on lanes
     // 3..7 of the group, where the beta pass with the default 25-value grid gives them no
     // weight row (h3_mixed).
+    // (CH candidates per chunk: CH / 8 column groups; tasks of a row group: 8 rows x CH / 8)
     const int nr = nz + 1;
-    const int ntask = ((nr + 7) >> 3) * 64;  // nz <= 36: at most 5 row groups, 320 tasks
+    const int ntask = ((nr + 7) >> 3) * CH;  // nz <= 36: at most 5 row groups, 5 CH tasks
+    bool inexact = false;
     for (int rnd = 0; rnd < 2; ++rnd) {
         const int idx = rnd == 0 ? (int)threadIdx.x : kThreads + ((int)threadIdx.x ^ 7);
         if (idx >= ntask) continue;
-        const int ri = ((idx >> 6) << 3) | (idx & 7), g8 = (idx >> 3) & 7;
+        const int ri = ((idx / CH) << 3) | (idx & 7), g8 = (idx % CH) >> 3;
         if (ri >= nr) continue;
         const int a = ri < nz ? ri : 36;
         const int ka = a < kZs ? h.koff[a] : -1;
@@ -910,9 +989,10 @@ __device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, int nz, float 
             }
             v[t] = x;
         }
-        if (INTFRAC) store8_int_frac<BF16>(t0, t1, t2, a, 8 * g8, 64, v);
-        else store8_split<BF16>(t0, t1, a, 8 * g8, 64, v);
+        if (INTFRAC) inexact |= store8_int_frac<BF16>(t0, t1, t2, a, 8 * g8, CH, v);
+        else inexact |= store8_split<BF16>(t0, t1, a, 8 * g8, CH, v);
     }
+    return inexact;
 }
 
 // H1 on tensor cores: D[a][b] = sum_j z'_ja z'_jb and D[a][36] = sum_j z'_ja, with
@@ -925,12 +1005,16 @@ __device__ __forceinline__ void stage_zt(Smem& sm, int c0, int n, int nz, float 
 // fraction split as the CUDA-core path, so the covariance keeps its precision through the
 // cancellation in Eq. (8).  Row 36 of the tiles is the constant one (n = 1, f = 0), so
 // column 36 of the integer sums holds sum_j n_a and (X + X^T)[a][36] holds sum_j f_a.
-template <bool BF16>
+// CH: candidates per chunk (32 or 64: the MMAs' K); the products are accumulated over the
+// same 16-candidate slices in the same order whatever CH, so the result does not depend on it.
+template <bool BF16, int CH>
 __device__ __noinline__ void h1_mixed(int M, int nz, float shift, uint32_t tmem, uint32_t mph) {
+    static_assert(CH == 32 || CH == 64, "H1 chunk");
+    constexpr int kRead = 256 / CH;  // chunks between integer readouts (256 candidates)
     Smem& sm = smem_ref();
     Hql& h = sm.hql;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int nchunks = (M + kCh - 1) / kCh;
+    const int nchunks = (M + CH - 1) / CH;
     const uint32_t idesc = tc::idesc_f16(64, 48, BF16);
     __syncthreads();  // the tiles share storage with buffers of the previous phase
     // both buffers (rows past the live features stay zero) and the integer sums
@@ -945,30 +1029,40 @@ __device__ __noinline__ void h1_mixed(int M, int nz, float shift, uint32_t tmem,
     // storage with the tiles)
     int(*nacc)[40] = reinterpret_cast<int(*)[40]>(tile(h, tl::kH1Sums));
     auto tb = [&](int b, int t) { return tile(h, (uint32_t)b * tl::kH1Buf + (uint32_t)t * tl::kH1Tile); };
-    stage_zt<BF16, true>(sm, 0, min(kCh, M), nz, shift, tb(0, 0), tb(0, 1), tb(0, 2));
+    // A chunk whose staged values are all integers (candidates made of received pixels only)
+    // has zero fractions: its X and Y products are left out.  xy_live: some chunk issued
+    // them (X and Y hold sums).
+    bool fr = stage_zt<BF16, true, CH>(sm, 0, min(CH, M), nz, shift, tb(0, 0), tb(0, 1), tb(0, 2));
+    bool xy_live = false;
     for (int ch = 0; ch < nchunks; ++ch) {
         const int b = ch & 1;
-        tiles_ready();
+        const bool frac = tiles_ready_or(fr);
+        const bool xy_acc = xy_live;
         mma_issue(sm, [&]() {
-            const uint32_t sbo = (64 / 8) * 128;
+            const uint32_t sbo = (CH / 8) * 128;
             const uint32_t an = tc::smem_addr(tb(b, 0)), ah = tc::smem_addr(tb(b, 1)),
                            al = tc::smem_addr(tb(b, 2));
-            for (int kk = 0; kk < 4; ++kk) {
+            for (int kk = 0; kk < CH / 16; ++kk) {
                 const uint32_t o = (uint32_t)kk * 256u;
                 const uint64_t dn = tc::smem_desc(an + o, 128, sbo), dh = tc::smem_desc(ah + o, 128, sbo),
                                dl = tc::smem_desc(al + o, 128, sbo);
-                tc::mma_f16(tmem, dn, dn, idesc, (ch & 3) != 0 || kk > 0);  // integer part: 4 chunks
-                tc::mma_f16(tmem + 64, dn, dh, idesc, ch > 0 || kk > 0);    // X = n (fh + fl)^T
-                tc::mma_f16(tmem + 64, dn, dl, idesc, true);
-                tc::mma_f16(tmem + 128, dh, dh, idesc, ch > 0 || kk > 0);   // Y = fh fh^T
+                tc::mma_f16(tmem, dn, dn, idesc, (ch % kRead) != 0 || kk > 0);  // integer part: 256 candidates
+                if (frac) {
+                    tc::mma_f16(tmem + 64, dn, dh, idesc, xy_acc || kk > 0);   // X = n (fh + fl)^T
+                    tc::mma_f16(tmem + 64, dn, dl, idesc, true);
+                    tc::mma_f16(tmem + 128, dh, dh, idesc, xy_acc || kk > 0);  // Y = fh fh^T
+                }
             }
+            sm.st[ST_MMA_FLOPS] += (frac ? 4ull : 1ull) * (CH / 16) * (2ull * 64 * 48 * 16);
         });
+        xy_live = xy_live || frac;
         if (ch + 1 < nchunks) {  // the next chunk, while these MMAs run
-            const int c1 = (ch + 1) * kCh;
-            stage_zt<BF16, true>(sm, c1, min(kCh, M - c1), nz, shift, tb(b ^ 1, 0), tb(b ^ 1, 1), tb(b ^ 1, 2));
+            const int c1 = (ch + 1) * CH;
+            fr = stage_zt<BF16, true, CH>(sm, c1, min(CH, M - c1), nz, shift, tb(b ^ 1, 0), tb(b ^ 1, 1),
+                                          tb(b ^ 1, 2));
         }
         mma_wait(sm, mph);
-        if (wid < 3 && ((ch & 3) == 3 || ch == nchunks - 1)) {  // exact sums into int32
+        if (wid < 3 && ((ch % kRead) == kRead - 1 || ch == nchunks - 1)) {  // exact sums into int32
             for (int c = 0; c < 5; ++c) {  // columns 0..39 in groups of 8 (36: column sums)
                 float D[8];
                 tc::tmem_ld8(tmem + tlane + 8 * c, D);
@@ -987,9 +1081,11 @@ __device__ __noinline__ void h1_mixed(int M, int nz, float shift, uint32_t tmem,
     static_assert(37 * 40 * sizeof(float) <= 2 * tl::kH1Buf, "X scratch inside the tiles");
     if (wid < 3) {
         for (int c = 0; c < 5; ++c) {
-            float X[8], Y[8];
-            tc::tmem_ld8(tmem + tlane + 64 + 8 * c, X);
-            tc::tmem_ld8(tmem + tlane + 128 + 8 * c, Y);
+            float X[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, Y[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (xy_live) {  // (CTA-uniform)
+                tc::tmem_ld8(tmem + tlane + 64 + 8 * c, X);
+                tc::tmem_ld8(tmem + tlane + 128 + 8 * c, Y);
+            }
             if (reader) {
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
@@ -1018,17 +1114,31 @@ __device__ __noinline__ void h1_mixed(int M, int nz, float shift, uint32_t tmem,
     __syncthreads();
 }
 
-// H2 on tensor cores: u_j = L^-1 (y_j - y0) for 64 candidates at a time, d_j = ||u_j||^2
-template <bool BF16>
-__device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem, uint32_t mph) {
+// H2 on tensor cores: u_j = L^-1 (y_j - y0) for CH candidates at a time (CH = 64: MMA
+// M = 64; CH = 128: M = 128), d_j = ||u_j||^2; u_j goes to ubuf (row j, 32 floats) for the
+// leave-one-out pass.  Each candidate's row is an independent product, so the result does not
+// depend on CH.  Layout of the region: A buffers (CH rows x K = 32, high and low halves, two
+// buffers), B = L^-1 (32 rows, high and low), then the staging rows of u (CH x 128 bytes).
+template <int CH>
+struct H2L {
+    static constexpr uint32_t kA = CH * 64, kABuf = 2 * kA, kB = 2 * kABuf, kBTile = 2048, kU = kB + 2 * kBTile;
+    static_assert(kU + CH * 128 <= tl::kRegion, "H2 tiles");
+};
+
+template <bool BF16, int CH>
+__device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem, uint32_t mph,
+                                       float* ubuf) {
+    static_assert(CH == 64 || CH == 128, "H2 chunk");
+    using L = H2L<CH>;
+    constexpr int kRowsW = CH / 4;  // accumulator rows per reading warp (warps 0..3)
     Smem& sm = smem_ref();
     Hql& h = sm.hql;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int nchunks = (M + kCh - 1) / kCh;
+    const int nchunks = (M + CH - 1) / CH;
     __syncthreads();  // the tiles share storage with buffers of the previous phase
     // B = L^-1 (32 rows k x 32 columns l), staged once
-    uint16_t* bhi = tile(h, tl::kH2B);
-    uint16_t* blo = tile(h, tl::kH2B + tl::kH2BTile);
+    uint16_t* bhi = tile(h, L::kB);
+    uint16_t* blo = tile(h, L::kB + L::kBTile);
     if (tid < 128) {
         const int k = (tid & 7) | ((tid >> 5) << 3), l8 = (tid >> 3) & 3;  // conflict-free stores
         float v[8];
@@ -1036,14 +1146,14 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
         for (int t = 0; t < 8; ++t) v[t] = h.Linv[k][8 * l8 + t];
         store8_split<BF16, true>(bhi, blo, k, 8 * l8, 32, v);
     }
-    // A = E (rows: candidates, columns: context) of chunk ch into buffer ch & 1, one task per
-    // thread (every row and column of the tile); a quarter-warp stores 8 consecutive rows of
+    // A = E (rows: candidates, columns: context) of chunk ch into buffer ch & 1: CH rows x 4
+    // column groups, CH / 64 tasks per thread; a quarter-warp stores 8 consecutive rows of
     // one column group (conflict-free)
     auto stage_a = [&](int ch) {
-        const int c0 = ch * kCh, n = min(kCh, M - c0);
-        const uint32_t o = (uint32_t)(ch & 1) * tl::kH2ABuf;
-        {  // 64 rows x 4 column groups: one task per thread
-            const int q = tid;
+        const int c0 = ch * CH, n = min(CH, M - c0);
+        const uint32_t o = (uint32_t)(ch & 1) * L::kABuf;
+#pragma unroll
+        for (int q = tid; q < 4 * CH; q += kThreads) {
             const int j = (q & 7) | ((q >> 5) << 3), l8 = (q >> 3) & 3;
             float v[8];
             const int base = j < n ? h.cand[c0 + j] : 0;
@@ -1052,23 +1162,40 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
                 const int l = 8 * l8 + t;
                 v[t] = (j < n && l < ny) ? (sm.S[base + h.off[l]] - shift) - h.ys[l] : 0.0f;
             }
-            store8_split<BF16, true>(tile(h, o), tile(h, o + tl::kH2A), j, 8 * l8, 32, v);
+            store8_split<BF16, true>(tile(h, o), tile(h, o + L::kA), j, 8 * l8, 32, v);
         }
     };
-    // d_j = ||u_j||^2 of chunk ch from tensor-memory columns 32 (ch & 1) .. +31; candidate
-    // j of the chunk in lane 16w + j%16 of warp w = j / 16 (M = 64 layout)
+    // d_j = ||u_j||^2 of chunk ch from tensor-memory columns 32 (ch & 1) .. +31.  Candidate
+    // j of the chunk: M = 64, lane 16w + j%16 of warp w = j / 16; M = 128, lane j%32 of warp
+    // w = j / 32.
     float lmin = INFINITY;
     auto read_d = [&](int ch) {
         if (wid < 4) {
-            const int c0 = ch * kCh, n = min(kCh, M - c0), j = 16 * wid + lane;
+            const int c0 = ch * CH, n = min(CH, M - c0), j = kRowsW * wid + lane;
+            const bool row_lane = kRowsW == 32 || lane < 16;
+            // the warp's rows of u go to global memory by one bulk copy (async proxy) from a
+            // shared staging area
+            float* us = reinterpret_cast<float*>(tile(h, L::kU)) + kRowsW * 32 * wid;
+            if (lane == 0) bulk_wait_read_all();  // the previous copy has read the staging rows
+            __syncwarp();
             float dd = 0.0f;
             for (int c = 0; c < 4; ++c) {  // groups of 8 columns (few live registers)
                 float u[8];
                 tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 32 * (ch & 1) + 8 * c, u);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) dd = __fmaf_rn(u[k], u[k], dd);
+                if (row_lane) {
+                    float* row = us + 32 * lane;
+                    *reinterpret_cast<float4*>(row + ubuf_pos(lane, 2 * c)) = make_float4(u[0], u[1], u[2], u[3]);
+                    *reinterpret_cast<float4*>(row + ubuf_pos(lane, 2 * c + 1)) = make_float4(u[4], u[5], u[6], u[7]);
+                }
             }
-            if (lane < 16 && j < n) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            const int nrows = min(kRowsW, n - kRowsW * wid);
+            if (lane == 0 && nrows > 0)
+                bulk_store(ubuf + (size_t)(c0 + kRowsW * wid) * kMaxNy, us, 128u * (unsigned)nrows);
+            if (row_lane && j < n) {
                 h.d[c0 + j] = dd;
                 lmin = fminf(lmin, dd);
             }
@@ -1076,30 +1203,34 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
     };
     stage_a(0);
     for (int ch = 0; ch < nchunks; ++ch) {
-        const uint32_t o = (uint32_t)(ch & 1) * tl::kH2ABuf;
+        const uint32_t o = (uint32_t)(ch & 1) * L::kABuf;
         tiles_ready();
         mma_issue(sm, [&]() {
-            mma3(tmem + 32 * (ch & 1), tile(h, o), tile(h, o + tl::kH2A), bhi, blo, 32,
-                 tc::idesc_f16(64, 32, BF16), false);
+            mma3(tmem + 32 * (ch & 1), tile(h, o), tile(h, o + L::kA), bhi, blo, 32,
+                 tc::idesc_f16(CH, 32, BF16), false);
+            sm.st[ST_MMA_FLOPS] += 6ull * (2ull * CH * 32 * 16);
         });
         if (ch + 1 < nchunks) stage_a(ch + 1);  // while the MMAs of chunk ch run
         if (ch > 0) read_d(ch - 1);            // (the other tensor-memory columns)
         mma_wait(sm, mph);
     }
     read_d(nchunks - 1);
+    if (wid < 4 && lane == 0) bulk_wait_all();  // u in global memory before the barrier
     tc::fence_before();
     __syncthreads();  // tensor memory read before the next pass's MMAs
     return lmin;
 }
 
 // H3 on tensor cores: D[b][k] = sum_j w_j(b) z'_j[k] with w_j(b) = exp(-(d_j - dmin)/(2 beta_b))
-template <bool BF16>
+// CH: candidates per chunk (32 or 64), as in h1_mixed; the result does not depend on it
+template <bool BF16, int CH>
 __device__ __noinline__ void h3_mixed(const KParams& P, int M, int nz, float shift, float dmin,
                                          uint32_t tmem, uint32_t mph) {
+    static_assert(CH == 32 || CH == 64, "H3 chunk");
     Smem& sm = smem_ref();
     Hql& h = sm.hql;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int nchunks = (M + kCh - 1) / kCh;
+    const int nchunks = (M + CH - 1) / CH;
     const int nb = P.nbeta;
     __syncthreads();  // the tiles share storage with buffers of the previous phase
     zero_region(h, tl::kH3Z, 2 * tl::kH3ZBuf);  // Z' rows past the live features stay zero
@@ -1107,15 +1238,17 @@ __device__ __noinline__ void h3_mixed(const KParams& P, int M, int nz, float shi
     auto zt = [&](int b, int t) { return tile(h, tl::kH3Z + (uint32_t)b * tl::kH3ZBuf + (uint32_t)t * tl::kH3ZTile); };
     auto wt = [&](int b, int t) { return tile(h, (uint32_t)b * tl::kH3WBuf + (uint32_t)t * tl::kH3W); };
     auto stage = [&](int ch) {
-        const int c0 = ch * kCh, n = min(kCh, M - c0), bf = ch & 1;
-        stage_zt<BF16, false>(sm, c0, n, nz, shift, zt(bf, 0), zt(bf, 1), nullptr);
-        // A = W (rows: beta, columns: candidates), 32 rows x 8 column groups; a quarter-warp
+        const int c0 = ch * CH, n = min(CH, M - c0), bf = ch & 1;
+        const bool zlo = stage_zt<BF16, false, CH>(sm, c0, n, nz, shift, zt(bf, 0), zt(bf, 1), nullptr);
+        // A = W (rows: beta, columns: candidates), 32 rows x CH/8 column groups; a quarter-warp
         // stores 8 consecutive rows of one column group (conflict-free)
-        {  // one task per thread; rows 24..31 (of which only 24 is live with the default
-           // 25-value grid) go to the first two warps, which take the second round of Z'
-           // tasks on other lanes (stage_zt), so that no thread stages three rows
+        if (tid < 4 * CH) {  // one task per thread; with CH = 64, rows 24..31 (of which only 24
+           // is live with the default 25-value grid) go to the first two warps, which take the
+           // second round of Z' tasks on other lanes (stage_zt), so that no thread stages
+           // three rows
             const int q = tid;
-            const int b = (q & 7) | (((q >> 6) ^ 3) << 3), g8 = (q >> 3) & 7;
+            const int b = CH == 64 ? ((q & 7) | (((q >> 6) ^ 3) << 3)) : ((q & 7) | ((q / CH) << 3));
+            const int g8 = (q % CH) >> 3;
             if (b < nb) {
                 float v[8];
                 const float ib = P.inv2beta[b];
@@ -1124,18 +1257,23 @@ __device__ __noinline__ void h3_mixed(const KParams& P, int M, int nz, float shi
                     const int j = 8 * g8 + t;
                     v[t] = j < n ? __expf(-(h.d[c0 + j] - dmin) * ib) : 0.0f;
                 }
-                store8_split<BF16>(wt(bf, 0), wt(bf, 1), b, 8 * g8, 64, v);
+                store8_split<BF16>(wt(bf, 0), wt(bf, 1), b, 8 * g8, CH, v);
             }
         }
+        return zlo;
     };
-    stage(0);
+    // a chunk of integer-valued candidates: Z' is exact in its high halves (|z'| <= 255), so
+    // the W-high x Z'-low product is left out
+    bool zlo = stage(0);
     for (int ch = 0; ch < nchunks; ++ch) {
         const int bf = ch & 1;
-        tiles_ready();
+        const bool zinexact = tiles_ready_or(zlo);
         mma_issue(sm, [&]() {
-            mma3(tmem, wt(bf, 0), wt(bf, 1), zt(bf, 0), zt(bf, 1), 64, tc::idesc_f16(64, 48, BF16), ch > 0);
+            mma3(tmem, wt(bf, 0), wt(bf, 1), zt(bf, 0), zt(bf, 1), CH, tc::idesc_f16(64, 48, BF16), ch > 0,
+                 !zinexact);
+            sm.st[ST_MMA_FLOPS] += (zinexact ? 3ull : 2ull) * (CH / 16) * (2ull * 64 * 48 * 16);
         });
-        if (ch + 1 < nchunks) stage(ch + 1);  // while the MMAs of chunk ch run
+        if (ch + 1 < nchunks) zlo = stage(ch + 1);  // while the MMAs of chunk ch run
         mma_wait(sm, mph);
     }
     if (wid < 2) {  // beta b in lane 16w + b%16 of warp w = b / 16 (M = 64 layout)
@@ -1240,7 +1378,7 @@ struct HqlOut {
 template <int MIXED>
 __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
                                         unsigned long long ymask, int ny, float mean, bool trace,
-                                        uint32_t mph) {
+                                        uint32_t mph, float* ubuf) {
     Smem& sm = smem_ref();
     Hql& h = sm.hql;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -1292,12 +1430,12 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
     const int nchunks = (M + kCh - 1) / kCh;
     SK_PHASE(PH_H0);
 
-    if (MIXED == 1) {
-        h1_mixed<true>(M, nz, shift, sm.tmem_base, mph);
-        mph ^= (uint32_t)(nchunks & 1);
-    } else if (MIXED == 2) {
-        h1_mixed<false>(M, nz, shift, sm.tmem_base, mph);
-        mph ^= (uint32_t)(nchunks & 1);
+    // chunks (and MMA commits) of the tensor-core passes at the tuned tile sizes
+    const int nch13 = (M + P.tile_h13 - 1) / P.tile_h13, nch2 = (M + P.tile_h2 - 1) / P.tile_h2;
+    if (MIXED) {
+        if (P.tile_h13 == 32) h1_mixed<MIXED == 1, 32>(M, nz, shift, sm.tmem_base, mph);
+        else h1_mixed<MIXED == 1, 64>(M, nz, shift, sm.tmem_base, mph);
+        mph ^= (uint32_t)(nch13 & 1);
     } else
     // H1: sums of z' and z' z'^T, z' = z - shift (Eq. (8)).  Thread (a, g) owns row a of the
     // product matrix over the candidates j = g (mod kG1).  Integer parts multiply and
@@ -1508,12 +1646,10 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
     // thread tile: 2 candidates x 4 whitened coordinates
     const int tj = (tid >> 3) * 2, tq = tid & 7;
     float lmin = INFINITY;
-    if (MIXED == 1) {
-        lmin = h2_mixed<true>(M, ny, shift, sm.tmem_base, mph);
-        mph ^= (uint32_t)(nchunks & 1);
-    } else if (MIXED == 2) {
-        lmin = h2_mixed<false>(M, ny, shift, sm.tmem_base, mph);
-        mph ^= (uint32_t)(nchunks & 1);
+    if (MIXED) {
+        if (P.tile_h2 == 128) lmin = h2_mixed<MIXED == 1, 128>(M, ny, shift, sm.tmem_base, mph, ubuf);
+        else lmin = h2_mixed<MIXED == 1, 64>(M, ny, shift, sm.tmem_base, mph, ubuf);
+        mph ^= (uint32_t)(nch2 & 1);
     } else {
         hql_stage(sm, 0, 0, min(kCh, M), shift);
         for (int ch = 0; ch < nchunks; ++ch) {
@@ -1521,6 +1657,12 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
             __syncthreads();
             float u0[4], u1[4];
             whiten_tile(h, buf, ny, tj, tq, u0, u1);
+            if (tj < n)
+                *reinterpret_cast<float4*>(ubuf + (size_t)(c0 + tj) * kMaxNy + ubuf_pos(c0 + tj, tq)) =
+                    make_float4(u0[0], u0[1], u0[2], u0[3]);
+            if (tj + 1 < n)
+                *reinterpret_cast<float4*>(ubuf + (size_t)(c0 + tj + 1) * kMaxNy + ubuf_pos(c0 + tj + 1, tq)) =
+                    make_float4(u1[0], u1[1], u1[2], u1[3]);
             float p0 = 0.0f, p1 = 0.0f;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -1561,12 +1703,10 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
     // j = g (mod kG3): acc[k] = sum_j w_j(b) z'_j[k] for the staged columns (x', y', 1).
     // Subset partial sums merge in double-float.
     const int nb = P.nbeta;
-    if (MIXED == 1) {
-        h3_mixed<true>(P, M, nz, shift, dmin, sm.tmem_base, mph);
-        mph ^= (uint32_t)(nchunks & 1);
-    } else if (MIXED == 2) {
-        h3_mixed<false>(P, M, nz, shift, dmin, sm.tmem_base, mph);
-        mph ^= (uint32_t)(nchunks & 1);
+    if (MIXED) {
+        if (P.tile_h13 == 32) h3_mixed<MIXED == 1, 32>(P, M, nz, shift, dmin, sm.tmem_base, mph);
+        else h3_mixed<MIXED == 1, 64>(P, M, nz, shift, dmin, sm.tmem_base, mph);
+        mph ^= (uint32_t)(nch13 & 1);
     } else {
         const int G3 = kThreads / nb;
         const int kql3 = (nz + 3) / 4;  // live column quads: 0 .. nz-1, and the constant (9)
@@ -1732,18 +1872,15 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
         for (int q = 0; q < per; ++q)
             if ((take >> q) & 1u) h.i0[pos++] = tid * per + q;
         __syncthreads();
-        // UI = L^-1 (y_i - y0), XI = x_i - shift
+        // UI = L^-1 (y_i - y0) of the members, as the distance pass formed them; XI = x_i - shift
         for (int idx = tid; idx < kMaxI0 * 36; idx += kThreads) {
             const int i = idx / 36, k = idx % 36;
             if (i >= n0) continue;
-            const int base = h.cand[h.i0[i]];
             if (k < 32) {
-                float u = 0.0f;
-                if (k < ny)
-                    for (int l = 0; l <= k; ++l)
-                        u = __fmaf_rn(h.Linv[k][l], (sm.S[base + h.off[l]] - shift) - h.ys[l], u);
-                h.UI[i][k] = u;
+                const int jj = h.i0[i];
+                h.UI[i][k] = __ldcg(ubuf + (size_t)jj * kMaxNy + ubuf_pos(jj, k >> 2) + (k & 3));
             } else {
+                const int base = h.cand[h.i0[i]];
                 const int a = k - 32;
                 h.XI[i][a] = sm.S[base + (a >> 1) * kReg + (a & 1) + 2 * kReg + 2] - shift;
             }
@@ -1758,8 +1895,9 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
     // Eq. (11) is linear in u, and G u_j = G L^-1 (y_j - y0) = K (y_j - y0), so four columns
     // of G u_j stand in for the 32 of u_j in the sums.  Each warp owns every 8th group of 32
     // candidates and runs without CTA barriers until the merge:
-    //   candidate mode (lane = candidate j): y_j - y0, u_j = L^-1 (y_j - y0), K (y_j - y0)
-    //     and x'_j into the warp's buffer;
+    //   candidate mode (lane = candidate j): u_j = L^-1 (y_j - y0) as the distance pass
+    //     formed it (read back from ubuf), K (y_j - y0) = G u_j and x'_j into the warp's
+    //     buffer;
     //   member mode (lane = member i < 32): the buffered candidates in turn, the squared
     //     whitened distance in packed two-lane FP32 over coordinate pairs;
     //   member 32 (|I0| = 33): each lane keeps the sums of its own candidates.
@@ -1782,44 +1920,30 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
         for (int bt = wid; bt < nbat; bt += kWarps) {
             const int j = 32 * bt + lane;
             const bool live = j < M;
-            {   // candidate mode
-                const int base = live ? h.cand[j] : 0;
-                float e[32];
+            {   // candidate mode: the group's u_j (from the distance pass) into the buffer,
+                // then per lane K (y_j - y0) = G u_j and x'_j
+                const float* src = ubuf + (size_t)32 * bt * kMaxNy;
+                const int nrow = min(32, M - 32 * bt);
 #pragma unroll
-                for (int l = 0; l < 32; ++l)
-                    e[l] = (live && l < ny) ? (sm.S[base + h.off[l]] - shift) - h.ys[l] : 0.0f;
-#pragma unroll
-                for (int r4 = 0; r4 < 8; ++r4) {  // u = L^-1 e (lower triangular, zero past Ny)
-                    float u[4];
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int r = 4 * r4 + t;
-                        float acc = 0.0f;
-#pragma unroll
-                        for (int q = 0; q <= r4; ++q) {
-                            const float4 lv = *reinterpret_cast<const float4*>(&h.Linv[r][4 * q]);
-                            acc = __fmaf_rn(lv.x, e[4 * q], acc);
-                            acc = __fmaf_rn(lv.y, e[4 * q + 1], acc);
-                            acc = __fmaf_rn(lv.z, e[4 * q + 2], acc);
-                            acc = __fmaf_rn(lv.w, e[4 * q + 3], acc);
-                        }
-                        u[t] = acc;
-                    }
-                    *reinterpret_cast<float4*>(&wb[lane][12 + 4 * r4]) = make_float4(u[0], u[1], u[2], u[3]);
+                for (int t = 0; t < 8; ++t) {  // 4 KB, coalesced; a quarter-warp fills one row
+                    const int idx = lane + 32 * t, row = idx >> 3, c4 = idx & 7;
+                    const float4 v = row < nrow ? __ldcg(reinterpret_cast<const float4*>(src + row * kMaxNy + ubuf_pos(row, c4)))
+                                                : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    *reinterpret_cast<float4*>(&wb[row][12 + 4 * c4]) = v;
                 }
-                float g[4];  // K e
+                __syncwarp();
+                const int base = live ? h.cand[j] : 0;
+                float g[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // G u_j over the live coordinate groups
+                for (int q = 0; q < nq; ++q) {
+                    const float4 uv = *reinterpret_cast<const float4*>(&wb[lane][12 + 4 * q]);
 #pragma unroll
-                for (int aa = 0; aa < 4; ++aa) {
-                    float g0 = 0.0f, g1 = 0.0f;
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 kv = *reinterpret_cast<const float4*>(&h.Kf[aa][4 * q]);
-                        g0 = __fmaf_rn(kv.x, e[4 * q], g0);
-                        g1 = __fmaf_rn(kv.y, e[4 * q + 1], g1);
-                        g0 = __fmaf_rn(kv.z, e[4 * q + 2], g0);
-                        g1 = __fmaf_rn(kv.w, e[4 * q + 3], g1);
+                    for (int aa = 0; aa < 4; ++aa) {
+                        const float4 gv = *reinterpret_cast<const float4*>(&h.G[aa][4 * q]);
+                        g[aa] = __fmaf_rn(gv.x, uv.x, g[aa]);
+                        g[aa] = __fmaf_rn(gv.y, uv.y, g[aa]);
+                        g[aa] = __fmaf_rn(gv.z, uv.z, g[aa]);
+                        g[aa] = __fmaf_rn(gv.w, uv.w, g[aa]);
                     }
-                    g[aa] = g0 + g1;
                 }
                 float x[4];
 #pragma unroll
@@ -1962,6 +2086,9 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
         sm.st[ST_HQL_M] += M;
         sm.st[ST_HQL_MNY] += (unsigned long long)M * ny;
         sm.st[ST_HQL_I0M] += (unsigned long long)n0 * M;
+        sm.st[ST_HQL_MNY2] += (unsigned long long)M * ny * ny;
+        sm.st[ST_HQL_NY3] += (unsigned long long)ny * ny * ny;
+        sm.st[ST_HQL_I0MNY] += (unsigned long long)n0 * M * ny;
 #ifdef SKMMSE_PHASE_CLOCKS
         {
             const long long t_ = clock64();
@@ -1970,11 +2097,11 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
         }
 #endif
         // algorithmic FP32 operations of this HQL estimate (one exp counts as one):
-        // covariance (upper C_YY and C_XY), two whitening passes with the distance,
-        // beta grid (exp + weighted sums of 4+Ny+1 columns), leave-one-out pass
+        // covariance (upper C_YY and C_XY), whitening with the distance, beta grid (exp +
+        // weighted sums of 4+Ny+1 columns), leave-one-out pass
         const unsigned long long Mu = M, nyu = ny, n0u = n0, nbu = P.nbeta;
         sm.st[ST_FLOPS] += Mu * (nyu * (nyu + 1) + 8 * nyu + 2 * (nyu + 4)) +
-                           2 * Mu * (nyu * (nyu + 1) + 2 * nyu) +
+                           Mu * (nyu * (nyu + 1) + 2 * nyu) +
                            nbu * Mu * (2 * (nyu + 5) + 3) +
                            n0u * Mu * (3 * nyu + 2 * (nyu + 5) + 3);
     }
@@ -2099,7 +2226,10 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
     uint32_t mph = 0;
     unsigned phase = 0;
     const int n_entries = W.counters[0];
-    if (tid == 0) sm.ph_t = clock64();
+    if (tid == 0) {
+        sm.ph_t = clock64();
+        sm.st[ST_T_FIRST_INV] = ~globaltimer_ns();  // (slots cleared before the barrier above)
+    }
 
     for (;;) {
         if (wid == 0) {
@@ -2206,18 +2336,19 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
         }
         __syncthreads();
 
+        const int npatch = __popcll(sm.unfilled);
+        if (wid == 0) fill_order(npatch);  // (read by warp 0 only)
         SK_PHASE(PH_STAGE);
         TraceRec* trace_base =
             (trace_on && F.trace) ? reinterpret_cast<TraceRec*>(F.trace) + (size_t)ent.z * 64 : nullptr;
-        const int npatch = __popcll(sm.unfilled);
         int step = 0;
         for (;;) {
             // Warp 0 alone runs the steps that stay in the base layer (Eq. (16), R3) back to
             // back; it stops at the first step that needs IDL and hands it to the CTA.
             if (wid == 0) {
-                long long n_brl = 0, n_empty = 0, flops = 0;
+                long long n_brl = 0, n_empty = 0, flops = 0, sum_ny = 0;
                 for (; step < npatch; ++step) {
-                    const int p = select_patch(sm, lane);
+                    const int p = sm.order[step];
                     const int pa = p >> 3, pb = p & 7;
                     const int wr = kMB + 2 * pa - 2, wc = kMB + 2 * pb - 2;
                     const CtxStats cs = ctx_stats(sm, wr, wc, lane);
@@ -2231,6 +2362,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                     SK_PHASE(PH_CTX);
                     if (cs.ny > 0 && cs.phi > P.t_phi) break;
                     const float xv = cs.ny == 0 ? 128.0f : cs.mean;
+                    const int layer = cs.ny == 0 ? L_EMPTY : L_BRL;
                     const int pr = wr + 2, pc = wc + 2;
                     if (lane < 4) {
                         float xw = fminf(fmaxf(xv, 0.0f), 255.0f);
@@ -2244,28 +2376,29 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                         sm.av[pr] |= 3ull << pc;
                         sm.av[pr + 1] |= 3ull << pc;
                         sm.unfilled &= ~(1ull << p);
-                        if (cs.ny == 0) ++n_empty;
+                        if (layer == L_EMPTY) ++n_empty;
                         else ++n_brl;
                         flops += 3ll * cs.ny;
-                        if (trace_base) {
-                            TraceRec t;
-                            t.mb = mb;
-                            t.step = (int16_t)step;
-                            t.patch = (int16_t)p;
-                            t.layer = (int8_t)(cs.ny == 0 ? L_EMPTY : L_BRL);
-                            t.ring = 0;
-                            t.beta_idx = -1;
-                            t.n0 = 0;
-                            t.ny = (int16_t)cs.ny;
-                            t.m = 0;
-                            t.phi = cs.phi;
-                            t.log_nu = -INFINITY;
-                            t.alpha = 0.0f;
-                            t.eps_best = 0.0f;
-                            for (int a = 0; a < 4; ++a) t.x[a] = fminf(fmaxf(xv, 0.0f), 255.0f);
-                            for (int q = 0; q < 36; ++q) t.i0[q] = 0xffff;
-                            trace_base[step] = t;
-                        }
+                        sum_ny += cs.ny;
+                    }
+                    if (trace_base && lane == 0) {
+                        TraceRec t;
+                        t.mb = mb;
+                        t.step = (int16_t)step;
+                        t.patch = (int16_t)p;
+                        t.layer = (int8_t)layer;
+                        t.ring = 0;
+                        t.beta_idx = -1;
+                        t.n0 = 0;
+                        t.ny = (int16_t)cs.ny;
+                        t.m = 0;
+                        t.phi = cs.phi;
+                        t.log_nu = -INFINITY;
+                        t.alpha = 0.0f;
+                        t.eps_best = 0.0f;
+                        for (int a = 0; a < 4; ++a) t.x[a] = fminf(fmaxf(xv, 0.0f), 255.0f);
+                        for (int q = 0; q < 36; ++q) t.i0[q] = 0xffff;
+                        trace_base[step] = t;
                     }
                     __syncwarp();
                     SK_PHASE(PH_BRL);
@@ -2276,6 +2409,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                     sm.st[ST_BRL] += n_brl;
                     sm.st[ST_EMPTY] += n_empty;
                     sm.st[ST_FLOPS] += flops;
+                    sm.st[ST_PATCH_NY] += sum_ny;
                 }
             }
             __syncthreads();
@@ -2334,7 +2468,8 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                     layer = L_HQL;
                     __syncthreads();  // IDL slots -> HQL scratch
                     const HqlOut o = hql_step<MIXED>(P, c.wr, c.wc, c.ymask, c.ny, c.mean,
-                                                     trace_base != nullptr, mph);
+                                                     trace_base != nullptr, mph,
+                                                     W.ubuf + (size_t)blockIdx.x * kUbufFloats);
                     mph = o.mph;
 #pragma unroll
                     for (int a = 0; a < 4; ++a) xhat[a] = o.x[a];
@@ -2364,6 +2499,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                 sm.unfilled &= ~(1ull << (c.pa * 8 + c.pb));
                 sm.st[ST_PATCH] += 1;
                 sm.st[ST_FLOPS] += 3ull * c.ny;  // context gather, flatness, mean
+                sm.st[ST_PATCH_NY] += c.ny;
                 sm.st[layer == L_IDL ? ST_IDL : layer == L_HQL ? ST_HQL : ST_NOCAND] += 1;
                 if (layer == L_IDL) sm.st[ST_RING0 + min(ring, 15)] += 1;
                 if (trace_base) {
@@ -2409,8 +2545,12 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
     tc::fence_after();
     if (MIXED && wid == 0) tc::tmem_dealloc(sm.tmem_base, kTmemCols<MIXED>);
     if (tid == 0 && sm.mma_err) atomicExch(&W.counters[2], 6);
-    for (int i = tid; i < kNStats; i += kThreads)
-        if (sm.st[i]) atomicAdd(&W.stats[i], sm.st[i]);
+    if (tid == 0) sm.st[ST_T_LAST] = globaltimer_ns();
+    __syncthreads();
+    for (int i = tid; i < kNStats; i += kThreads) {
+        if (i == ST_T_FIRST_INV || i == ST_T_LAST) atomicMax(&W.stats[i], sm.st[i]);
+        else if (sm.st[i]) atomicAdd(&W.stats[i], sm.st[i]);
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -2611,7 +2751,8 @@ __global__ void __launch_bounds__(kThreads) queue_fill_kernel(WorkDev W, int sup
 namespace sk {
 static_assert(sizeof(Smem) <= 113 * 1024, "two CTAs per SM");
 static_assert(offsetof(Hql, mx) % 16 == 0 && sizeof(Hql::mx) == 4 * 128 * 64 * 2, "tensor-core tiles");
-static_assert(offsetof(Hql, Z) % 16 == 0 && offsetof(Hql, Linv) % 16 == 0 &&
+static_assert((offsetof(Smem, hql) + offsetof(Hql, mx)) % 128 == 0, "tensor-core tiles on 128-byte lines");
+static_assert(offsetof(Hql, Z) % 16 == 0 && offsetof(Hql, Linv) % 16 == 0 && offsetof(Hql, G) % 16 == 0 &&
                   offsetof(Hql, ys) % 16 == 0 && offsetof(Smem, hql) % 16 == 0,
               "float4 operands");
 }  // namespace sk

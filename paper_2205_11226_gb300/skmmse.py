@@ -29,7 +29,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported frame shape", 3: "unsu
           6: "dependency wait timed out on the device", 7: "unsupported precision or flag",
           8: "frame exceeds the static scratch of the no-allocation entry point"}
 NOALLOC_MAX_MBS = 8192
-ABI_VERSION = 2
+ABI_VERSION = 3
 
 
 class Params(ctypes.Structure):
@@ -51,6 +51,17 @@ class Frame(ctypes.Structure):
     ]
 
 
+class Config(ctypes.Structure):
+    """skmmse_config: persistent CTAs per SM and the tensor-core tile sizes."""
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("tile_cov", ctypes.c_int), ("tile_dist", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+TUNE_MAX_OPTIONS = 8
+
+
 class Stats(ctypes.Structure):
     _fields_ = [
         ("n_lost_mbs", ctypes.c_longlong), ("n_patches", ctypes.c_longlong),
@@ -59,12 +70,18 @@ class Stats(ctypes.Structure):
         ("idl_ring_hist", ctypes.c_longlong * 16), ("idl_cand_evals", ctypes.c_longlong),
         ("idl_ny_evals", ctypes.c_longlong), ("hql_cands", ctypes.c_longlong),
         ("hql_ny_cands", ctypes.c_longlong), ("hql_i0_cands", ctypes.c_longlong),
-        ("alg_flops", ctypes.c_longlong), ("n_beta", ctypes.c_longlong), ("error", ctypes.c_int), ("pad", ctypes.c_int),
+        ("alg_flops", ctypes.c_longlong), ("hql_ny2_cands", ctypes.c_longlong), ("hql_ny3", ctypes.c_longlong),
+        ("hql_i0_ny_cands", ctypes.c_longlong), ("patch_ny", ctypes.c_longlong), ("mma_flops", ctypes.c_longlong),
+        ("t_first_inv_ns", ctypes.c_longlong), ("t_last_ns", ctypes.c_longlong),
+        ("n_beta", ctypes.c_longlong), ("error", ctypes.c_int), ("pad", ctypes.c_int),
     ]
 
     def as_dict(self) -> dict:
-        return {k: (list(getattr(self, k)) if k == "idl_ring_hist" else int(getattr(self, k)))
-                for k, _ in self._fields_ if k != "pad"}
+        d = {k: (list(getattr(self, k)) if k == "idl_ring_hist" else int(getattr(self, k)))
+             for k, _ in self._fields_ if k != "pad"}
+        # the concealment kernel's resident interval on the device (global timer, ns)
+        d["t_first_ns"] = (~d.pop("t_first_inv_ns")) & (2 ** 64 - 1) if d["t_last_ns"] else 0
+        return d
 
 
 TRACE_DTYPE = np.dtype([
@@ -79,7 +96,8 @@ EXPORTS = ["skmmse_abi_version", "skmmse_struct_size", "skmmse_status_str", "skm
            "skmmse_read_stats", "skmmse_read_phase_clocks", "skmmse_conceal_noalloc",
            "skmmse_probe_peaks",
            "skmmse_graph_create", "skmmse_graph_launch", "skmmse_graph_read_stats",
-           "skmmse_graph_destroy", "skmmse_autotune", "skmmse_set_ctas_per_sm"]
+           "skmmse_graph_destroy", "skmmse_autotune", "skmmse_set_ctas_per_sm", "skmmse_set_config",
+           "skmmse_get_config"]
 
 _lib = None
 
@@ -135,7 +153,12 @@ def load(path: str = LIB_PATH):
     lib.skmmse_graph_destroy.argtypes = [vp]
     lib.skmmse_autotune.restype = ci
     lib.skmmse_autotune.argtypes = [vp, ctypes.POINTER(Frame), ci, ctypes.POINTER(Params), ci, vp,
-                                    ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ci)]
+                                    ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_float),
+                                    ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    lib.skmmse_set_config.restype = ci
+    lib.skmmse_set_config.argtypes = [vp, ctypes.POINTER(Config)]
+    lib.skmmse_get_config.restype = ci
+    lib.skmmse_get_config.argtypes = [vp, ctypes.POINTER(Frame), ci, ctypes.POINTER(Params), ctypes.POINTER(Config)]
     lib.skmmse_set_ctas_per_sm.restype = ci
     lib.skmmse_set_ctas_per_sm.argtypes = [vp, ci]
     lib.skmmse_probe_peaks.restype = ci
@@ -147,6 +170,7 @@ def load(path: str = LIB_PATH):
     assert lib.skmmse_struct_size(1) == ctypes.sizeof(Stats), "stats layout"
     assert lib.skmmse_struct_size(2) == ctypes.sizeof(Params), "params layout"
     assert lib.skmmse_struct_size(3) == ctypes.sizeof(Frame), "frame layout"
+    assert lib.skmmse_struct_size(4) == ctypes.sizeof(Config), "config layout"
     _lib = lib
     return lib
 
@@ -279,18 +303,37 @@ class Context:
 
     def autotune(self, frames, masks, p: Params | None = None, *, outs=None, reps: int = 2,
                  stream=None) -> dict:
-        """Pick the persistent CTAs per SM for this batch by timing; returns the timings."""
+        """Time every launch configuration on this batch and keep the fastest for its shape
+        class.  Returns the options timed, their mean milliseconds and the chosen one."""
         import torch
         p = p if p is not None else params()
         if outs is None:
             outs = [torch.empty_like(f) for f in frames]
         descs = self._descs(frames, masks, outs)
-        ms = (ctypes.c_float * 8)()
-        best = ctypes.c_int()
+        opts = (Config * TUNE_MAX_OPTIONS)()
+        ms = (ctypes.c_float * TUNE_MAX_OPTIONS)()
+        nopt, best = ctypes.c_int(), ctypes.c_int()
         _check(self._lib.skmmse_autotune(self._h, descs, len(frames), ctypes.byref(p), reps,
-                                         _stream_handle(stream), ms, ctypes.byref(best)),
-               "skmmse_autotune")
-        return {"ctas_per_sm": best.value, "ms": [v for v in ms if v > 0]}
+                                         _stream_handle(stream), opts, ms, ctypes.byref(nopt),
+                                         ctypes.byref(best)), "skmmse_autotune")
+        options = [{**opts[i].as_dict(), "ms": float(ms[i])} for i in range(nopt.value)]
+        chosen = options[best.value]
+        return {"options": options, "best": chosen, "ctas_per_sm": chosen["ctas_per_sm"],
+                "ms": [o["ms"] for o in options]}
+
+    def set_config(self, ctas_per_sm: int = 0, tile_cov: int = 64, tile_dist: int = 64):
+        """The configuration of shape classes the autotuner has not timed."""
+        c = Config(ctas_per_sm, tile_cov, tile_dist)
+        _check(self._lib.skmmse_set_config(self._h, ctypes.byref(c)), "skmmse_set_config")
+
+    def get_config(self, frames, masks, p: Params | None = None) -> dict:
+        """The configuration a batch call with these frames would use."""
+        p = p if p is not None else params()
+        descs = self._descs(frames, masks, frames)
+        c = Config()
+        _check(self._lib.skmmse_get_config(self._h, descs, len(frames), ctypes.byref(p), ctypes.byref(c)),
+               "skmmse_get_config")
+        return c.as_dict()
 
     def set_ctas_per_sm(self, k: int):
         _check(self._lib.skmmse_set_ctas_per_sm(self._h, int(k)), "skmmse_set_ctas_per_sm")

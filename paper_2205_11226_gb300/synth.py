@@ -188,7 +188,8 @@ def blocks_of(px_lost: np.ndarray) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------------------
-# the five workloads (sizes as stated in the design document)
+# the five workloads: one 256x256 frame with one lost block; the 512x512 checkerboard; a
+# 1920x1080 frame with runs of lost blocks; the 64-frame batch of mixed sizes; the stream
 
 def workload_single(seed: int = 0):
     """256x256 frame, one lost block at pixel (112, 112) = block (7, 7)."""

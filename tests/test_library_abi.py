@@ -32,11 +32,12 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_struct_layouts(lib):
-    assert lib.skmmse_abi_version() == 2
+    assert lib.skmmse_abi_version() == skmmse.ABI_VERSION == 3
     assert lib.skmmse_struct_size(0) == skmmse.TRACE_DTYPE.itemsize == 120
     assert lib.skmmse_struct_size(1) == ctypes.sizeof(skmmse.Stats)
     assert lib.skmmse_struct_size(2) == ctypes.sizeof(skmmse.Params)
     assert lib.skmmse_struct_size(3) == ctypes.sizeof(skmmse.Frame)
+    assert lib.skmmse_struct_size(4) == ctypes.sizeof(skmmse.Config) == 12
     assert lib.skmmse_struct_size(9) == -1
 
 
@@ -94,3 +95,16 @@ def test_argument_validation_before_any_device_call(lib):
     assert call(pitch=32) == SHAPE and call(out_pitch=32) == SHAPE
     assert call(f32=OUT + 2) == ALIGN
     assert call(w=4096, h=4096, pitch=4096, out_pitch=4096) == TOO_LARGE
+
+
+def test_noalloc_scratch_size_stated_in_the_header():
+    # the static scratch of skmmse_conceal_noalloc, as the header states it (the library
+    # pins the same figure with a static_assert on its layout)
+    text = open(os.path.join(ROOT, "include", "skmmse.h")).read()
+    nbytes = int(re.search(r"#define SKMMSE_NOALLOC_SCRATCH_BYTES (\d+)", text).group(1))
+    ctas = int(re.search(r"#define SKMMSE_NOALLOC_MAX_CTAS (\d+)", text).group(1))
+    mbs = int(re.search(r"#define SKMMSE_NOALLOC_MAX_MBS (\d+)", text).group(1))
+    assert mbs == skmmse.NOALLOC_MAX_MBS and ctas == 128
+    # per CTA: the whitened vectors of one HQL step, 1849 candidates x 32 floats
+    assert nbytes > ctas * 1849 * 32 * 4 + mbs * 256 * 4
+    assert f"{nbytes / 1e6:.1f} MB" in text

@@ -29,13 +29,19 @@ def _noalloc(lib, frame, mask, p, out, out_f32):
     return rc, st.as_dict()
 
 
-def test_noalloc_matches_context_entry_point_twice(gpu_lib):
+@pytest.mark.parametrize("precision", [skmmse.FP32, skmmse.MIXED_FP16])
+def test_noalloc_matches_context_entry_point_twice(gpu_lib, precision):
+    """Calls in a row on one shared scratch: a frame, a larger one, then a smaller one again
+    (the last call leaves entries, values and done flags of the larger frame past its own
+    blocks).  Each result equals the context entry point's, bit for bit: the same kernels
+    run the same arithmetic per block, whatever the number of persistent CTAs."""
     import torch
     cases = [synth.workload_checkerboard(11, 256, 192),
-             (synth.make_frame(320, 240, 12, fine_texture=True), synth.loss_runs(320, 240, 13, 0.25))]
-    p = skmmse.params("efficient")
+             (synth.make_frame(320, 240, 12, fine_texture=True), synth.loss_runs(320, 240, 13, 0.25)),
+             (synth.make_frame(160, 96, 14), synth.loss_runs(160, 96, 15, 0.3))]
+    p = skmmse.params("efficient", precision=precision)
     ctx = skmmse.Context()
-    for f_np, m_np in cases:  # two calls in a row, different frames
+    for f_np, m_np in cases:
         f = torch.from_numpy(f_np).cuda()
         m = torch.from_numpy(m_np).cuda()
         ref_out, ref_f32, ref_st = ctx.conceal(f, m, p, out_f32=True, stats=True)
@@ -45,9 +51,11 @@ def test_noalloc_matches_context_entry_point_twice(gpu_lib):
         torch.cuda.synchronize()
         assert rc == 0, skmmse.STATUS.get(rc, rc)
         assert st["n_lost_mbs"] == int(m_np.sum()) == ref_st["n_lost_mbs"]
+        assert st["n_hql"] == ref_st["n_hql"] and st["n_idl"] == ref_st["n_idl"]
         lost = torch.from_numpy(synth.lost_pixel_mask(m_np, f_np.shape[1], f_np.shape[0])).cuda()
         err = (out_f32 - ref_f32)[lost].abs().max().item()
         assert err <= TOL_FP32, err
+        assert torch.equal(out_f32[lost], ref_f32[lost])
         assert torch.equal(out, ref_out)
     ctx.close()
 

@@ -266,8 +266,8 @@ void skmmse_graph_destroy(skmmse_graph* g);
      ctas_per_sm  persistent CTAs per SM, 1 .. the occupancy maximum (2), 0 = the maximum;
                   fewer CTAs give each block more of its SM and shorten dependency chains,
                   more run more blocks at once;
-     tile_cov     candidates per chunk of the HQL covariance and beta-grid passes (the
-                  MMAs' K, Eqs. (8)-(10)): 32 or 64;
+     tile_cov     candidates per chunk of the HQL covariance pass (the MMAs' K, Eq. (8)):
+                  32 or 64;
      tile_dist    candidates per tile of the whitened-distance pass (the MMA's M, Eq. (6)
                   with C_YY): 64 or 128.
    The tiles apply to the mixed precisions; the FP32 path ignores them. */

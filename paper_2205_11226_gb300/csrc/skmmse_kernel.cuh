@@ -104,7 +104,7 @@ struct KParams {
     unsigned flags;
     int mixed;            // 0: FP32 on the CUDA cores; 1: BF16, 2: FP16 tensor-core contractions
     unsigned claim_idle_limit;  // polls without progress before a CTA gives up claiming
-    int tile_h13;         // candidates per chunk of the covariance and beta passes: 32 or 64
+    int tile_h13;         // candidates per chunk of the covariance pass: 32 or 64
     int tile_h2;          // candidates per tile of the distance pass: 64 or 128 (MMA M)
 };
 
@@ -323,21 +323,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map,
 
 __device__ __forceinline__ void tmap_acquire(const CUtensorMap* map) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
-}
-
-// bulk copy shared -> global (async proxy), completion by bulk groups
-__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, unsigned bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
-                 "r"(smem_u32(ssrc)), "r"(bytes)
-                 : "memory");
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_read_all() {  // sources read: staging reusable
-    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_all() {  // writes performed, then visible to loads
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-    asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 // the GPU's global timer (nanoseconds), comparable across the CTAs and launches of a device
@@ -894,12 +879,10 @@ __device__ __forceinline__ void zero_region(Hql& h, uint32_t off, uint32_t bytes
     for (int i = threadIdx.x; i < (int)(bytes / 16); i += kThreads) p[i] = make_uint4(0, 0, 0, 0);
 }
 
-// D (+)= A * B^T over K columns with split operands (issued by one thread).  b_lo_zero: every
-// low half of B is zero (B held exactly by its high halves), so the A-high x B-low product
-// is left out.
+// D (+)= A * B^T over K columns with split operands (issued by one thread)
 __device__ __forceinline__ void mma3(uint32_t tmem, const uint16_t* ahi, const uint16_t* alo,
                                      const uint16_t* bhi, const uint16_t* blo, int K, uint32_t idesc,
-                                     bool accumulate, bool b_lo_zero = false) {
+                                     bool accumulate) {
     const uint32_t sbo = (uint32_t)(K / 8) * 128u;
     const uint32_t a0 = tc::smem_addr(ahi), a1 = tc::smem_addr(alo);
     const uint32_t b0 = tc::smem_addr(bhi), b1 = tc::smem_addr(blo);
@@ -907,8 +890,7 @@ __device__ __forceinline__ void mma3(uint32_t tmem, const uint16_t* ahi, const u
         const uint32_t o = (uint32_t)kk * 256u;
         tc::mma_f16(tmem, tc::smem_desc(a0 + o, 128, sbo), tc::smem_desc(b0 + o, 128, sbo), idesc,
                     accumulate || kk > 0);
-        if (!b_lo_zero)
-            tc::mma_f16(tmem, tc::smem_desc(a0 + o, 128, sbo), tc::smem_desc(b1 + o, 128, sbo), idesc, true);
+        tc::mma_f16(tmem, tc::smem_desc(a0 + o, 128, sbo), tc::smem_desc(b1 + o, 128, sbo), idesc, true);
         tc::mma_f16(tmem, tc::smem_desc(a1 + o, 128, sbo), tc::smem_desc(b0 + o, 128, sbo), idesc, true);
     }
 }
@@ -1173,11 +1155,10 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
         if (wid < 4) {
             const int c0 = ch * CH, n = min(CH, M - c0), j = kRowsW * wid + lane;
             const bool row_lane = kRowsW == 32 || lane < 16;
-            // the warp's rows of u go to global memory by one bulk copy (async proxy) from a
-            // shared staging area
+            // the warp's rows of u pass through shared memory, so that the global stores are
+            // whole 128-byte rows (8 lanes per row; a bulk copy through the async proxy
+            // measured slower: its proxy fence waits behind the MMAs in flight)
             float* us = reinterpret_cast<float*>(tile(h, L::kU)) + kRowsW * 32 * wid;
-            if (lane == 0) bulk_wait_read_all();  // the previous copy has read the staging rows
-            __syncwarp();
             float dd = 0.0f;
             for (int c = 0; c < 4; ++c) {  // groups of 8 columns (few live registers)
                 float u[8];
@@ -1190,11 +1171,15 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
                     *reinterpret_cast<float4*>(row + ubuf_pos(lane, 2 * c + 1)) = make_float4(u[4], u[5], u[6], u[7]);
                 }
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-            const int nrows = min(kRowsW, n - kRowsW * wid);
-            if (lane == 0 && nrows > 0)
-                bulk_store(ubuf + (size_t)(c0 + kRowsW * wid) * kMaxNy, us, 128u * (unsigned)nrows);
+#pragma unroll
+            for (int t = 0; t < kRowsW / 4; ++t) {  // rows x 8 float4, 4 rows per instruction
+                const int idx = lane + 32 * t, r = idx >> 3, c4 = idx & 7;
+                if (kRowsW * wid + r < n)
+                    *reinterpret_cast<float4*>(ubuf + (size_t)(c0 + kRowsW * wid + r) * kMaxNy + 4 * c4) =
+                        *reinterpret_cast<const float4*>(us + 32 * r + 4 * c4);
+            }
+            __syncwarp();  // the staging rows take the next chunk
             if (row_lane && j < n) {
                 h.d[c0 + j] = dd;
                 lmin = fminf(lmin, dd);
@@ -1215,22 +1200,19 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
         mma_wait(sm, mph);
     }
     read_d(nchunks - 1);
-    if (wid < 4 && lane == 0) bulk_wait_all();  // u in global memory before the barrier
     tc::fence_before();
     __syncthreads();  // tensor memory read before the next pass's MMAs
     return lmin;
 }
 
 // H3 on tensor cores: D[b][k] = sum_j w_j(b) z'_j[k] with w_j(b) = exp(-(d_j - dmin)/(2 beta_b))
-// CH: candidates per chunk (32 or 64), as in h1_mixed; the result does not depend on it
-template <bool BF16, int CH>
+template <bool BF16>
 __device__ __noinline__ void h3_mixed(const KParams& P, int M, int nz, float shift, float dmin,
                                          uint32_t tmem, uint32_t mph) {
-    static_assert(CH == 32 || CH == 64, "H3 chunk");
     Smem& sm = smem_ref();
     Hql& h = sm.hql;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int nchunks = (M + CH - 1) / CH;
+    const int nchunks = (M + kCh - 1) / kCh;
     const int nb = P.nbeta;
     __syncthreads();  // the tiles share storage with buffers of the previous phase
     zero_region(h, tl::kH3Z, 2 * tl::kH3ZBuf);  // Z' rows past the live features stay zero
@@ -1238,17 +1220,15 @@ __device__ __noinline__ void h3_mixed(const KParams& P, int M, int nz, float shi
     auto zt = [&](int b, int t) { return tile(h, tl::kH3Z + (uint32_t)b * tl::kH3ZBuf + (uint32_t)t * tl::kH3ZTile); };
     auto wt = [&](int b, int t) { return tile(h, (uint32_t)b * tl::kH3WBuf + (uint32_t)t * tl::kH3W); };
     auto stage = [&](int ch) {
-        const int c0 = ch * CH, n = min(CH, M - c0), bf = ch & 1;
-        const bool zlo = stage_zt<BF16, false, CH>(sm, c0, n, nz, shift, zt(bf, 0), zt(bf, 1), nullptr);
-        // A = W (rows: beta, columns: candidates), 32 rows x CH/8 column groups; a quarter-warp
+        const int c0 = ch * kCh, n = min(kCh, M - c0), bf = ch & 1;
+        stage_zt<BF16, false, kCh>(sm, c0, n, nz, shift, zt(bf, 0), zt(bf, 1), nullptr);
+        // A = W (rows: beta, columns: candidates), 32 rows x 8 column groups; a quarter-warp
         // stores 8 consecutive rows of one column group (conflict-free)
-        if (tid < 4 * CH) {  // one task per thread; with CH = 64, rows 24..31 (of which only 24
-           // is live with the default 25-value grid) go to the first two warps, which take the
-           // second round of Z' tasks on other lanes (stage_zt), so that no thread stages
-           // three rows
+        {  // one task per thread; rows 24..31 (of which only 24 is live with the default
+           // 25-value grid) go to the first two warps, which take the second round of Z'
+           // tasks on other lanes (stage_zt), so that no thread stages three rows
             const int q = tid;
-            const int b = CH == 64 ? ((q & 7) | (((q >> 6) ^ 3) << 3)) : ((q & 7) | ((q / CH) << 3));
-            const int g8 = (q % CH) >> 3;
+            const int b = (q & 7) | (((q >> 6) ^ 3) << 3), g8 = (q >> 3) & 7;
             if (b < nb) {
                 float v[8];
                 const float ib = P.inv2beta[b];
@@ -1257,23 +1237,19 @@ __device__ __noinline__ void h3_mixed(const KParams& P, int M, int nz, float shi
                     const int j = 8 * g8 + t;
                     v[t] = j < n ? __expf(-(h.d[c0 + j] - dmin) * ib) : 0.0f;
                 }
-                store8_split<BF16>(wt(bf, 0), wt(bf, 1), b, 8 * g8, CH, v);
+                store8_split<BF16>(wt(bf, 0), wt(bf, 1), b, 8 * g8, 64, v);
             }
         }
-        return zlo;
     };
-    // a chunk of integer-valued candidates: Z' is exact in its high halves (|z'| <= 255), so
-    // the W-high x Z'-low product is left out
-    bool zlo = stage(0);
+    stage(0);
     for (int ch = 0; ch < nchunks; ++ch) {
         const int bf = ch & 1;
-        const bool zinexact = tiles_ready_or(zlo);
+        tiles_ready();
         mma_issue(sm, [&]() {
-            mma3(tmem, wt(bf, 0), wt(bf, 1), zt(bf, 0), zt(bf, 1), CH, tc::idesc_f16(64, 48, BF16), ch > 0,
-                 !zinexact);
-            sm.st[ST_MMA_FLOPS] += (zinexact ? 3ull : 2ull) * (CH / 16) * (2ull * 64 * 48 * 16);
+            mma3(tmem, wt(bf, 0), wt(bf, 1), zt(bf, 0), zt(bf, 1), 64, tc::idesc_f16(64, 48, BF16), ch > 0);
+            sm.st[ST_MMA_FLOPS] += 12ull * (2ull * 64 * 48 * 16);
         });
-        if (ch + 1 < nchunks) zlo = stage(ch + 1);  // while the MMAs of chunk ch run
+        if (ch + 1 < nchunks) stage(ch + 1);  // while the MMAs of chunk ch run
         mma_wait(sm, mph);
     }
     if (wid < 2) {  // beta b in lane 16w + b%16 of warp w = b / 16 (M = 64 layout)
@@ -1430,7 +1406,8 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
     const int nchunks = (M + kCh - 1) / kCh;
     SK_PHASE(PH_H0);
 
-    // chunks (and MMA commits) of the tensor-core passes at the tuned tile sizes
+    // chunks (and MMA commits) of the tensor-core passes at the tuned tile sizes (the beta
+    // pass keeps kCh)
     const int nch13 = (M + P.tile_h13 - 1) / P.tile_h13, nch2 = (M + P.tile_h2 - 1) / P.tile_h2;
     if (MIXED) {
         if (P.tile_h13 == 32) h1_mixed<MIXED == 1, 32>(M, nz, shift, sm.tmem_base, mph);
@@ -1704,9 +1681,8 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
     // Subset partial sums merge in double-float.
     const int nb = P.nbeta;
     if (MIXED) {
-        if (P.tile_h13 == 32) h3_mixed<MIXED == 1, 32>(P, M, nz, shift, dmin, sm.tmem_base, mph);
-        else h3_mixed<MIXED == 1, 64>(P, M, nz, shift, dmin, sm.tmem_base, mph);
-        mph ^= (uint32_t)(nch13 & 1);
+        h3_mixed<MIXED == 1>(P, M, nz, shift, dmin, sm.tmem_base, mph);
+        mph ^= (uint32_t)(nchunks & 1);
     } else {
         const int G3 = kThreads / nb;
         const int kql3 = (nz + 3) / 4;  // live column quads: 0 .. nz-1, and the constant (9)

@@ -29,3 +29,15 @@ def test_oversized_request_rejected():
     a.arrive(req(0, 1))
     with pytest.raises(ValueError):
         a.admit()
+
+
+def test_resident_concurrency_of_launch_intervals():
+    from paper_2205_11226_gb300.serving import resident_concurrency
+    # [0, 10] and [5, 15]: busy 15, two resident for 5 -> mean (5 + 2*5 + 5) / 15
+    r = resident_concurrency([(0, 10), (5, 15)])
+    assert r["max_resident_launches"] == 2
+    assert abs(r["mean_resident_launches"] - 20 / 15) < 1e-12
+    # disjoint intervals never overlap; the gap is not busy time
+    r = resident_concurrency([(0, 10), (20, 30)])
+    assert r["max_resident_launches"] == 1 and r["mean_resident_launches"] == 1.0
+    assert abs(r["device_busy_s"] - 20e-9) < 1e-18

@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--serve-oracle-every", type=int, default=50,
                     help="serving: the oracle is timed on every n-th request (0: not at all)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the occupancy-maximal grid")
+    ap.add_argument("--launch-config", default=None,
+                    help="ctas_per_sm,tile_cov,tile_dist: use this launch configuration instead of "
+                         "autotuning (e.g. 2,64,128)")
     ap.add_argument("--no-graph", action="store_true",
                     help="time direct skmmse_conceal_batch calls instead of the CUDA graph")
     ap.add_argument("--precision", choices=list(PRECISIONS), default="fp16",
@@ -486,7 +489,9 @@ def run_ours(args):
     any_px = any(m.shape == f.shape for f, m in zip(frames, masks))
 
     tuned = None
-    if not args.no_autotune:  # CTAs per SM and tensor-core tiles, picked by timing this batch
+    if args.launch_config:
+        ctx.set_config(*[int(v) for v in args.launch_config.split(",")])
+    elif not args.no_autotune:  # CTAs per SM and tensor-core tiles, picked by timing this batch
         tuned = ctx.autotune(fd, md, p, outs=od, reps=1, stream=stream)
     graph = None
     if not args.no_graph:     # the batch call (queue construction + persistent kernel) as a graph

@@ -93,6 +93,13 @@ typedef enum { SKMMSE_EXPRESS = 0, SKMMSE_EFFICIENT = 1, SKMMSE_EXCELLENT = 2 } 
    block (the working CTAs take the rest), sets the device error word and returns
    SKMMSE_ERR_TIMEOUT, and the context stays usable.  Not for production use. */
 #define SKMMSE_FLAG_SHORT_WAITS 8u
+/* IDL distances on tensor cores (mixed precision only; ignored in FP32): when a patch's
+   first ring does not reach T_nu, the distances of Eq. (15) for all 43 x 43 window
+   positions are formed in one pass of Toeplitz products on tcgen05 (per window row r, the
+   region's rows r.. against the template row, high and low 16-bit halves, and the squared
+   region against the context mask), and the later rings read them.  Exact for integer
+   templates and windows; otherwise within the split's precision.  Off by default. */
+#define SKMMSE_FLAG_IDL_TC 16u
 
 typedef struct {
     float t_phi;        /* flatness threshold T_phi, Eq. (17) / Table I; BRL iff phi <= T_phi */

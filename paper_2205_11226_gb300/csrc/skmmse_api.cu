@@ -23,6 +23,7 @@ using sk::WorkDev;
 static_assert(sizeof(sk::TraceRec) == sizeof(skmmse_trace_rec), "trace layout");
 // the counter slots map onto the leading long long fields of skmmse_stats, in order
 static_assert(offsetof(skmmse_stats, n_beta) == sizeof(long long) * sk::ST_COUNT, "stats layout");
+static_assert(SKMMSE_FLAG_IDL_TC == sk::kFlagIdlTc, "flag value");
 
 struct skmmse_context {
     int device = 0;
@@ -74,7 +75,8 @@ skmmse_status validate_params(const skmmse_params* p) {
     if (p->precision != SKMMSE_FP32 && p->precision != SKMMSE_MIXED_BF16 &&
         p->precision != SKMMSE_MIXED_FP16)
         return SKMMSE_ERR_ARG;
-    if (p->flags & ~(SKMMSE_FLAG_TRACE | SKMMSE_FLAG_FORCE | SKMMSE_FLAG_QUANTIZE | SKMMSE_FLAG_SHORT_WAITS))
+    if (p->flags & ~(SKMMSE_FLAG_TRACE | SKMMSE_FLAG_FORCE | SKMMSE_FLAG_QUANTIZE | SKMMSE_FLAG_SHORT_WAITS |
+                     SKMMSE_FLAG_IDL_TC))
         return SKMMSE_ERR_ARG;
     if ((p->flags & SKMMSE_FLAG_FORCE) && !(p->flags & SKMMSE_FLAG_TRACE)) return SKMMSE_ERR_ARG;
     return SKMMSE_OK;

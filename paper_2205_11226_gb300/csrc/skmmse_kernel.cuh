@@ -549,8 +549,14 @@ struct IdlOut {
     int r;      // 1 accepted, 0 not accepted, -1 no candidate
 };
 
+template <bool BF16>
+__device__ __noinline__ void idl_tc_distances(int wr, int wc, unsigned long long ymask, float cen,
+                                              uint32_t tmem, uint32_t mph);
+constexpr unsigned kFlagIdlTc = 16u;  // SKMMSE_FLAG_IDL_TC
+
+template <int MIXED>
 __device__ __forceinline__ IdlOut idl_step(const KParams& P, int wr, int wc,
-                                        unsigned long long ymask, int ny, float mean) {
+                                        unsigned long long ymask, int ny, float mean, uint32_t mph) {
     Smem& sm = smem_ref();
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     StepCtx c;
@@ -575,10 +581,16 @@ __device__ __forceinline__ IdlOut idl_step(const KParams& P, int wr, int wc,
     int accepted = 0, k = 1;
     float lognu = -INFINITY;
     int total_cnt = 0;
+    // with SKMMSE_FLAG_IDL_TC (mixed precision), the rings after the first take their
+    // distances from one tensor-core pass over every window position
+    const bool tc_rings = MIXED != 0 && (P.flags & kFlagIdlTc) != 0u;
     for (k = 1; k <= P.nrings; ++k) {
         const int rin = (k - 1) * P.ring_step, rout = k * P.ring_step;
         const int side = 2 * rout + 1, inner = 2 * rin + 1;
         const int npos = side * side - inner * inner;
+        if (MIXED != 0 && tc_rings && k == 2)
+            idl_tc_distances<MIXED == 1>(c.wr, c.wc, c.ymask, cen, sm.tmem_base, mph);
+        const bool from_d = tc_rings && k >= 2;
         for (int i = tid; i < npos; i += kThreads) {
             int dy, dx;
             annulus_pos(i, rin, rout, &dy, &dx);
@@ -586,7 +598,7 @@ __device__ __forceinline__ IdlOut idl_step(const KParams& P, int wr, int wc,
             if (u < 0 || v < 0 || u >= kNpos || v >= kNpos) continue;
             if (!cand_valid(sm, c, u, v)) continue;
             const int base = u * kReg + v;
-            const float d = ctx_dist(sm.S, c, base);
+            const float d = from_d ? sm.hql.d[u * kNpos + v] : ctx_dist(sm.S, c, base);
             const float* X = &sm.S[base + 2 * kReg + 2];
             online_add(-d * inv_h, X[0] - cen, X[1] - cen, X[kReg] - cen, X[kReg + 1] - cen, m,
                        s0, sx);
@@ -1261,6 +1273,112 @@ __device__ __noinline__ void h3_mixed(const KParams& P, int M, int nz, float shi
 #pragma unroll
                 for (int t = 0; t < 8; ++t)
                     if (8 * c + t < 37) h.accBd[b][8 * c + t] = df_make(D[t]);
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+}
+
+// IDL distances of every candidate window on tensor cores (mixed precision, option
+// SKMMSE_FLAG_IDL_TC): for the rings after the first, the distances of Eq. (15) of all
+// 43 x 43 window positions in one pass.  With S' = S - cen, y0' = y0 - cen and m the context
+// mask of the 6x6 window,
+//   d[u][v] = sum_{r,c} m[r][c] (S'[u+r][v+c] - y0'[r][c])^2
+//           = sum_r sum_x S'[u+r][x] (-2 T[r][x-v]) + S'[u+r][x]^2 M[r][x-v]  +  sum m y0'^2,
+// T = m y0', M = m (zero outside 0 <= x-v <= 5): for each window row r a Toeplitz product
+// A_r B_r^T with A_r[u][x] = S'[u+r][x] (u: M = 64 rows, 43 live; x: K = 48) and B_r[v][x]
+// (v: N = 48 rows, 43 live).  S' and T are split into high and low 16-bit halves (three
+// MMAs), S'^2 too (two MMAs against the exact 0/1 mask); all accumulate in one FP32
+// tensor-memory tile.  Integer contexts and windows (received pixels) are exact in both
+// formats.  d goes to h.d[u * 43 + v].
+namespace tli {
+constexpr uint32_t kA = 64 * 48 * 2, kB = 48 * 48 * 2;  // tile bytes
+constexpr uint32_t kAhi = 0, kAlo = kA, kQhi = 2 * kA, kQlo = 3 * kA, kBhi = 4 * kA, kBlo = 4 * kA + kB,
+                   kMk = 4 * kA + 2 * kB, kEnd = 4 * kA + 3 * kB;
+static_assert(kEnd <= tl::kRegion && kBhi % 128 == 0 && kBlo % 128 == 0 && kMk % 128 == 0, "IDL tiles");
+}  // namespace tli
+
+template <bool BF16>
+__device__ __noinline__ void idl_tc_distances(int wr, int wc, unsigned long long ymask, float cen,
+                                              uint32_t tmem, uint32_t mph) {
+    Smem& sm = smem_ref();
+    Hql& h = sm.hql;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t idesc = tc::idesc_f16(64, 48, BF16);
+    float y2 = 0.0f;  // sum m y0'^2 (every thread, the same order)
+#pragma unroll
+    for (int k = 0; k < 36; ++k)
+        if ((ymask >> k) & 1ull) {
+            const float t = sm.S[(wr + k / 6) * kReg + wc + k % 6] - cen;
+            y2 = __fmaf_rn(t, t, y2);
+        }
+    __syncthreads();  // the tiles share storage with the IDL slots' neighbours of the union
+    for (int r = 0; r < 6; ++r) {
+        // A rows u (64 x 6 column groups) and B rows v (48 x 6 column groups); a quarter-warp
+        // stores 8 consecutive rows of one column group (conflict-free)
+        for (int q = tid; q < 64 * 6 + 48 * 6; q += kThreads) {
+            const bool isA = q < 64 * 6;
+            const int qq = isA ? q : q - 64 * 6;
+            const int row = (qq & 7) | ((qq / 48) << 3), g = (qq >> 3) % 6;
+            float v[8];
+            if (isA) {
+                const int sr = row + r;
+                float v2[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const float x = (row < kNpos && sr < kReg) ? sm.S[sr * kReg + 8 * g + t] - cen : 0.0f;
+                    v[t] = x;
+                    v2[t] = __fmul_rn(x, x);
+                }
+                store8_split<BF16>(tile(h, tli::kAhi), tile(h, tli::kAlo), row, 8 * g, 48, v);
+                store8_split<BF16>(tile(h, tli::kQhi), tile(h, tli::kQlo), row, 8 * g, 48, v2);
+            } else {
+                float mk[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int c = 8 * g + t - row;  // window column of x = 8g + t for v = row
+                    const bool on = row < kNpos && c >= 0 && c < 6 && ((ymask >> (6 * r + c)) & 1ull);
+                    v[t] = on ? -2.0f * (sm.S[(wr + r) * kReg + wc + c] - cen) : 0.0f;
+                    mk[t] = on ? 1.0f : 0.0f;
+                }
+                store8_split<BF16>(tile(h, tli::kBhi), tile(h, tli::kBlo), row, 8 * g, 48, v);
+                uint32_t w[4];
+#pragma unroll
+                for (int p2 = 0; p2 < 4; ++p2) w[p2] = pack_int2<BF16>(mk[2 * p2], mk[2 * p2 + 1]);
+                const uint32_t off = tc::kmajor_offset(row, 8 * g, 48) >> 1;
+                *reinterpret_cast<uint4*>(tile(h, tli::kMk) + off) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        tiles_ready();
+        mma_issue(sm, [&]() {
+            mma3(tmem, tile(h, tli::kAhi), tile(h, tli::kAlo), tile(h, tli::kBhi), tile(h, tli::kBlo), 48, idesc,
+                 r > 0);
+            const uint32_t sbo = (48 / 8) * 128;
+            const uint32_t q0 = tc::smem_addr(tile(h, tli::kQhi)), q1 = tc::smem_addr(tile(h, tli::kQlo));
+            const uint32_t bm = tc::smem_addr(tile(h, tli::kMk));
+            for (int kk = 0; kk < 3; ++kk) {
+                const uint32_t o = (uint32_t)kk * 256u;
+                const uint64_t dm = tc::smem_desc(bm + o, 128, sbo);
+                tc::mma_f16(tmem, tc::smem_desc(q0 + o, 128, sbo), dm, idesc, true);
+                tc::mma_f16(tmem, tc::smem_desc(q1 + o, 128, sbo), dm, idesc, true);
+            }
+            sm.st[ST_MMA_FLOPS] += 15ull * (2ull * 64 * 48 * 16);
+        });
+        mma_wait(sm, mph);  // (the tiles take the next row)
+    }
+    // d of row u from tensor-memory lane 32 (u / 16) + u % 16 (M = 64 layout)
+    if (wid < 4) {
+        const int u = 16 * wid + lane;
+        for (int c = 0; c < 6; ++c) {
+            float D[8];
+            tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 8 * c, D);
+            if (lane < 16 && u < kNpos) {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int v = 8 * c + t;
+                    if (v < kNpos) h.d[u * kNpos + v] = fmaxf(D[t] + y2, 0.0f);
+                }
             }
         }
     }
@@ -2421,7 +2539,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                 for (int t = 0; t < 36; ++t) sm.tr.i0[t] = 0xffff;
             }
             {
-                const IdlOut io = idl_step(P, c.wr, c.wc, c.ymask, c.ny, c.mean);
+                const IdlOut io = idl_step<MIXED>(P, c.wr, c.wc, c.ymask, c.ny, c.mean, mph);
                 const int r = io.r;
                 ring = io.ring;
                 lognu = io.lognu;

@@ -23,6 +23,7 @@ FLAG_TRACE = 1
 FLAG_FORCE = 2
 FLAG_QUANTIZE = 4
 FLAG_SHORT_WAITS = 8
+FLAG_IDL_TC = 16
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported frame shape", 3: "unsupported alignment",
           4: "device memory allocation failed", 5: "CUDA runtime error",

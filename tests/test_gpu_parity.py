@@ -181,3 +181,38 @@ def test_quantize_inloop(gpu_ctx, precision, tol):
     assert np.array_equal(g["out_f32"], np.rint(g["out_f32"]))
     lost = synth.lost_pixel_mask(m, f.shape[1], f.shape[0])  # out_f32: concealed pixels only
     assert np.array_equal(g["out"][lost].astype(np.float32), g["out_f32"][lost])
+
+
+# ---------------------------------------------------------------------------------------
+# IDL distances on tensor cores (SKMMSE_FLAG_IDL_TC): the rings after the first read the
+# distances of one Toeplitz-product pass over every window position
+
+@pytest.mark.parametrize("precision", [skmmse.MIXED_FP16, skmmse.MIXED_BF16])
+def test_idl_distances_on_tensor_cores(gpu_ctx, precision):
+    # T_nu = 10: many patches need rings past the first, where the tensor-core distances act
+    f = synth.make_frame(256, 160, 8, fine_texture=True)
+    m = synth.loss_runs(256, 160, 3, 0.25)
+    p = skmmse.params("efficient", t_nu=10.0, precision=precision, flags=skmmse.FLAG_IDL_TC)
+    rep, gpu, orc = check(f, m, p, gpu_ctx, tol=TOL_MIXED)
+    assert sum(gpu["stats"]["idl_ring_hist"][2:]) > 50, gpu["stats"]["idl_ring_hist"]
+    # against the CUDA-core distances on the same inputs (teacher-forced): the same decisions
+    # up to near-ties, the estimates within the mixed tolerance
+    p0 = skmmse.params("efficient", t_nu=10.0, precision=precision)
+    g0, _ = run_forced(f, m, p0, gpu_ctx)
+    same = (gpu["trace"]["layer"] == g0["trace"]["layer"]) & (gpu["trace"]["ring"] == g0["trace"]["ring"])
+    assert same.mean() > 0.99
+    d = np.abs(gpu["trace"]["x"] - g0["trace"]["x"]).max(-1)[same]
+    assert d.max() <= TOL_MIXED
+
+
+@pytest.mark.parametrize("precision", [skmmse.MIXED_FP16, skmmse.MIXED_BF16])
+def test_idl_tc_all_rings_before_hql(gpu_ctx, precision):
+    # forced HQL: every step evaluates all rings (tensor-core distances for rings 2..7) and
+    # then HQL, whose estimate does not depend on the IDL distances: outputs equal the
+    # CUDA-core run's bit for bit
+    f, m = synth.workload_single(1)
+    base = dict(t_phi=-1.0, t_nu=1e30, precision=precision)
+    a = skmmse.conceal_numpy(f, m, skmmse.params("efficient", flags=skmmse.FLAG_IDL_TC, **base), ctx=gpu_ctx)
+    b = skmmse.conceal_numpy(f, m, skmmse.params("efficient", **base), ctx=gpu_ctx)
+    assert a["stats"]["n_hql"] == 64
+    assert np.array_equal(a["out_f32"], b["out_f32"])

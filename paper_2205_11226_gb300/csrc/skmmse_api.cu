@@ -162,7 +162,12 @@ skmmse_config resolve_config(const skmmse_context* c, const skmmse_frame* frames
 // kernel instantiations: FP32, and tensor-core contractions with BF16 or FP16 operands
 
 void launch_conceal(const KParams& kp, const WorkDev& w, unsigned grid, cudaStream_t stream) {
-    if (kp.mixed == 1)
+    const bool tc = (kp.flags & SKMMSE_FLAG_IDL_TC) != 0u;  // (mixed precision only)
+    if (kp.mixed == 1 && tc)
+        sk::conceal_kernel<1, true><<<grid, sk::kThreads, sizeof(sk::Smem), stream>>>(w, kp);
+    else if (kp.mixed == 2 && tc)
+        sk::conceal_kernel<2, true><<<grid, sk::kThreads, sizeof(sk::Smem), stream>>>(w, kp);
+    else if (kp.mixed == 1)
         sk::conceal_kernel<1><<<grid, sk::kThreads, sizeof(sk::Smem), stream>>>(w, kp);
     else if (kp.mixed == 2)
         sk::conceal_kernel<2><<<grid, sk::kThreads, sizeof(sk::Smem), stream>>>(w, kp);
@@ -178,6 +183,12 @@ cudaError_t set_kernel_attributes() {
         e = cudaFuncSetAttribute(sk::conceal_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(sk::Smem));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(sk::conceal_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(sk::Smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sk::conceal_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(sk::Smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sk::conceal_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(sk::Smem));
     return e;
 }
 

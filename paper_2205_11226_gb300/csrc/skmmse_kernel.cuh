@@ -50,7 +50,8 @@ constexpr int kNPhase = 16;
 // whitened context differences u_j = L^-1 (y_j - y0) of one HQL step, kept in global
 // memory (per persistent CTA) from the distance pass for the leave-one-out pass: row j of
 // 32 floats, its float4 number c4 at float offset ubuf_pos(j, c4) (XOR-swizzled, the
-// order of the shared staging rows that feed the bulk copies)
+// order of the shared staging rows).  Only the ceil(Ny/4) live groups are written: the
+// coordinates past Ny are exact zeros (L^-1 is zero there), and readers take them as such.
 constexpr int kUbufFloats = kNcand * kMaxNy;
 __host__ __device__ __forceinline__ int ubuf_pos(int j, int c4) { return 4 * (c4 ^ (j & 7)); }
 
@@ -554,7 +555,9 @@ __device__ __noinline__ void idl_tc_distances(int wr, int wc, unsigned long long
                                               uint32_t tmem, uint32_t mph);
 constexpr unsigned kFlagIdlTc = 16u;  // SKMMSE_FLAG_IDL_TC
 
-template <int MIXED>
+// IDLTC: the kernel instantiation with the tensor-core distances for the rings after the
+// first (SKMMSE_FLAG_IDL_TC); the default instantiation carries none of that code
+template <int MIXED, bool IDLTC>
 __device__ __forceinline__ IdlOut idl_step(const KParams& P, int wr, int wc,
                                         unsigned long long ymask, int ny, float mean, uint32_t mph) {
     Smem& sm = smem_ref();
@@ -581,16 +584,16 @@ __device__ __forceinline__ IdlOut idl_step(const KParams& P, int wr, int wc,
     int accepted = 0, k = 1;
     float lognu = -INFINITY;
     int total_cnt = 0;
-    // with SKMMSE_FLAG_IDL_TC (mixed precision), the rings after the first take their
-    // distances from one tensor-core pass over every window position
-    const bool tc_rings = MIXED != 0 && (P.flags & kFlagIdlTc) != 0u;
+    // IDLTC (mixed precision): the rings after the first take their distances from one
+    // tensor-core pass over every window position
     for (k = 1; k <= P.nrings; ++k) {
         const int rin = (k - 1) * P.ring_step, rout = k * P.ring_step;
         const int side = 2 * rout + 1, inner = 2 * rin + 1;
         const int npos = side * side - inner * inner;
-        if (MIXED != 0 && tc_rings && k == 2)
-            idl_tc_distances<MIXED == 1>(c.wr, c.wc, c.ymask, cen, sm.tmem_base, mph);
-        const bool from_d = tc_rings && k >= 2;
+        if constexpr (IDLTC && MIXED != 0) {
+            if (k == 2) idl_tc_distances<MIXED == 1>(c.wr, c.wc, c.ymask, cen, sm.tmem_base, mph);
+        }
+        const bool from_d = IDLTC && k >= 2;
         for (int i = tid; i < npos; i += kThreads) {
             int dy, dx;
             annulus_pos(i, rin, rout, &dy, &dx);
@@ -1125,30 +1128,35 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
     static_assert(CH == 64 || CH == 128, "H2 chunk");
     using L = H2L<CH>;
     constexpr int kRowsW = CH / 4;  // accumulator rows per reading warp (warps 0..3)
+    // live coordinates: groups of 8 tensor-memory columns and of 4 stored floats (past Ny the
+    // whitened coordinates are exact zeros)
+    const int n8 = (ny + 7) >> 3, nq = (ny + 3) >> 2;
+    // K = N = 16 when Ny <= 16: the dropped K slices and output columns hold exact zeros, so
+    // the products are the same bit for bit, at half the MMAs and operand staging
+    const int KH = ny <= 16 ? 16 : 32, G = KH >> 3, gsh = KH == 16 ? 4 : 5;
     Smem& sm = smem_ref();
     Hql& h = sm.hql;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nchunks = (M + CH - 1) / CH;
     __syncthreads();  // the tiles share storage with buffers of the previous phase
-    // B = L^-1 (32 rows k x 32 columns l), staged once
+    // B = L^-1 (KH rows k x KH columns l), staged once
     uint16_t* bhi = tile(h, L::kB);
     uint16_t* blo = tile(h, L::kB + L::kBTile);
-    if (tid < 128) {
-        const int k = (tid & 7) | ((tid >> 5) << 3), l8 = (tid >> 3) & 3;  // conflict-free stores
+    if (tid < KH * G) {
+        const int k = (tid & 7) | ((tid >> gsh) << 3), l8 = (tid >> 3) & (G - 1);  // conflict-free stores
         float v[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) v[t] = h.Linv[k][8 * l8 + t];
-        store8_split<BF16, true>(bhi, blo, k, 8 * l8, 32, v);
+        store8_split<BF16, true>(bhi, blo, k, 8 * l8, KH, v);
     }
-    // A = E (rows: candidates, columns: context) of chunk ch into buffer ch & 1: CH rows x 4
-    // column groups, CH / 64 tasks per thread; a quarter-warp stores 8 consecutive rows of
-    // one column group (conflict-free)
+    // A = E (rows: candidates, columns: context) of chunk ch into buffer ch & 1: CH rows x G
+    // column groups; a quarter-warp stores 8 consecutive rows of one column group
+    // (conflict-free)
     auto stage_a = [&](int ch) {
         const int c0 = ch * CH, n = min(CH, M - c0);
         const uint32_t o = (uint32_t)(ch & 1) * L::kABuf;
-#pragma unroll
-        for (int q = tid; q < 4 * CH; q += kThreads) {
-            const int j = (q & 7) | ((q >> 5) << 3), l8 = (q >> 3) & 3;
+        for (int q = tid; q < G * CH; q += kThreads) {
+            const int j = (q & 7) | ((q >> gsh) << 3), l8 = (q >> 3) & (G - 1);
             float v[8];
             const int base = j < n ? h.cand[c0 + j] : 0;
 #pragma unroll
@@ -1156,7 +1164,7 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
                 const int l = 8 * l8 + t;
                 v[t] = (j < n && l < ny) ? (sm.S[base + h.off[l]] - shift) - h.ys[l] : 0.0f;
             }
-            store8_split<BF16, true>(tile(h, o), tile(h, o + L::kA), j, 8 * l8, 32, v);
+            store8_split<BF16, true>(tile(h, o), tile(h, o + L::kA), j, 8 * l8, KH, v);
         }
     };
     // d_j = ||u_j||^2 of chunk ch from tensor-memory columns 32 (ch & 1) .. +31.  Candidate
@@ -1172,7 +1180,7 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
             // measured slower: its proxy fence waits behind the MMAs in flight)
             float* us = reinterpret_cast<float*>(tile(h, L::kU)) + kRowsW * 32 * wid;
             float dd = 0.0f;
-            for (int c = 0; c < 4; ++c) {  // groups of 8 columns (few live registers)
+            for (int c = 0; c < n8; ++c) {  // live groups of 8 columns (few live registers)
                 float u[8];
                 tc::tmem_ld8(tmem + ((uint32_t)(32 * wid) << 16) + 32 * (ch & 1) + 8 * c, u);
 #pragma unroll
@@ -1186,10 +1194,11 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
             __syncwarp();
 #pragma unroll
             for (int t = 0; t < kRowsW / 4; ++t) {  // rows x 8 float4, 4 rows per instruction
-                const int idx = lane + 32 * t, r = idx >> 3, c4 = idx & 7;
-                if (kRowsW * wid + r < n)
-                    *reinterpret_cast<float4*>(ubuf + (size_t)(c0 + kRowsW * wid + r) * kMaxNy + 4 * c4) =
-                        *reinterpret_cast<const float4*>(us + 32 * r + 4 * c4);
+                const int idx = lane + 32 * t, r = idx >> 3, p4 = idx & 7;  // p4: physical position
+                const int c4 = p4 ^ (r & 7);                                 // its logical group
+                if (kRowsW * wid + r < n && c4 < nq)
+                    *reinterpret_cast<float4*>(ubuf + (size_t)(c0 + kRowsW * wid + r) * kMaxNy + 4 * p4) =
+                        *reinterpret_cast<const float4*>(us + 32 * r + 4 * p4);
             }
             __syncwarp();  // the staging rows take the next chunk
             if (row_lane && j < n) {
@@ -1203,9 +1212,9 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
         const uint32_t o = (uint32_t)(ch & 1) * L::kABuf;
         tiles_ready();
         mma_issue(sm, [&]() {
-            mma3(tmem + 32 * (ch & 1), tile(h, o), tile(h, o + L::kA), bhi, blo, 32,
-                 tc::idesc_f16(CH, 32, BF16), false);
-            sm.st[ST_MMA_FLOPS] += 6ull * (2ull * CH * 32 * 16);
+            mma3(tmem + 32 * (ch & 1), tile(h, o), tile(h, o + L::kA), bhi, blo, KH,
+                 tc::idesc_f16(CH, KH, BF16), false);
+            sm.st[ST_MMA_FLOPS] += 3ull * (KH / 16) * (2ull * CH * KH * 16);
         });
         if (ch + 1 < nchunks) stage_a(ch + 1);  // while the MMAs of chunk ch run
         if (ch > 0) read_d(ch - 1);            // (the other tensor-memory columns)
@@ -1752,10 +1761,11 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
             __syncthreads();
             float u0[4], u1[4];
             whiten_tile(h, buf, ny, tj, tq, u0, u1);
-            if (tj < n)
+            if (4 * tq >= ny) {  // coordinates past Ny: zero, not stored
+            } else if (tj < n)
                 *reinterpret_cast<float4*>(ubuf + (size_t)(c0 + tj) * kMaxNy + ubuf_pos(c0 + tj, tq)) =
                     make_float4(u0[0], u0[1], u0[2], u0[3]);
-            if (tj + 1 < n)
+            if (4 * tq < ny && tj + 1 < n)
                 *reinterpret_cast<float4*>(ubuf + (size_t)(c0 + tj + 1) * kMaxNy + ubuf_pos(c0 + tj + 1, tq)) =
                     make_float4(u1[0], u1[1], u1[2], u1[3]);
             float p0 = 0.0f, p1 = 0.0f;
@@ -1972,7 +1982,7 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
             if (i >= n0) continue;
             if (k < 32) {
                 const int jj = h.i0[i];
-                h.UI[i][k] = __ldcg(ubuf + (size_t)jj * kMaxNy + ubuf_pos(jj, k >> 2) + (k & 3));
+                h.UI[i][k] = k < ny ? __ldcg(ubuf + (size_t)jj * kMaxNy + ubuf_pos(jj, k >> 2) + (k & 3)) : 0.0f;
             } else {
                 const int base = h.cand[h.i0[i]];
                 const int a = k - 32;
@@ -2021,8 +2031,9 @@ __device__ __noinline__ HqlOut hql_step(const KParams& P, int wr, int wc,
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {  // 4 KB, coalesced; a quarter-warp fills one row
                     const int idx = lane + 32 * t, row = idx >> 3, c4 = idx & 7;
-                    const float4 v = row < nrow ? __ldcg(reinterpret_cast<const float4*>(src + row * kMaxNy + ubuf_pos(row, c4)))
-                                                : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    const float4 v = (row < nrow && c4 < nq)
+                                         ? __ldcg(reinterpret_cast<const float4*>(src + row * kMaxNy + ubuf_pos(row, c4)))
+                                         : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                     *reinterpret_cast<float4*>(&wb[row][12 + 4 * c4]) = v;
                 }
                 __syncwarp();
@@ -2297,7 +2308,7 @@ __device__ __noinline__ void release_dependants(const WorkDev& W, const FrameDev
 template <int MIXED>
 constexpr uint32_t kTmemCols = 256u;
 
-template <int MIXED>
+template <int MIXED, bool IDLTC = false>
 __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_constant__ WorkDev W,
                                                               const __grid_constant__ KParams P) {
     Smem& sm = smem_ref();
@@ -2539,7 +2550,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                 for (int t = 0; t < 36; ++t) sm.tr.i0[t] = 0xffff;
             }
             {
-                const IdlOut io = idl_step<MIXED>(P, c.wr, c.wc, c.ymask, c.ny, c.mean, mph);
+                const IdlOut io = idl_step<MIXED, IDLTC>(P, c.wr, c.wc, c.ymask, c.ny, c.mean, mph);
                 const int r = io.r;
                 ring = io.ring;
                 lognu = io.lognu;

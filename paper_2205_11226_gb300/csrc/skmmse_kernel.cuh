@@ -134,7 +134,8 @@ struct WorkDev {
     unsigned* done;           // per entry: 0 pending, 1 done, 2 done with error
     float* vals;              // per entry: 256 unrounded values of the block
     unsigned long long* stats;
-    int* height_of_mb;        // per block of all frames: longest chain of dependants (-1 received)
+    int* height_of_mb;        // per block of all frames: longest chain of dependants (-1 received,
+                              // kIsolated for a lost block with no lost neighbour)
     int* bk_off;              // per bucket: number of entries, then the bucket's first entry
     int* bk_cnt;              // per bucket: entries handed out while filling (= its size after)
     int* bk_head;             // per bucket: ready entries claimed
@@ -2687,11 +2688,22 @@ __global__ void __launch_bounds__(kThreads) px_block_flags_kernel(const __grid_c
 // Work queue.  A lost block depends on its lost neighbours earlier in raster order (left,
 // top-left, top, top-right) when concealed pixels are support.  The blocks of a call are
 // grouped into buckets by their height, the length of the longest chain of blocks that
-// depend on them (0 for a block nothing waits for); bucket key = nbk - 1 - height, so low
-// keys hold the blocks that head the longest chains.  A block becomes ready when its last
-// dependency is done and is then published in its bucket; a free CTA claims a ready block
-// of the lowest live key (highest height first: list scheduling by critical path).  A CTA
-// only ever claims ready blocks, so no CTA holds an SM while it waits for a dependency.
+// depend on them (0 for a block nothing waits for); bucket key = nbk - 2 - height, so low
+// keys hold the blocks that head the longest chains.  Blocks with no lost neighbour at all
+// take the last bucket, nbk - 1, after every block of a loss cluster: a block's cost is not
+// known before it runs (it is set by how many of its steps reach HQL), and run this way the
+// clusters' blocks, which carry the chains and on average more HQL steps, do not end up
+// behind the isolated ones at the end of the call, where one expensive block left alone
+// holds the whole call.  A block becomes ready when its last dependency is done and is
+// then published in its bucket; a free CTA claims a ready block of the lowest live key
+// (highest height first: list scheduling by critical path).  A CTA only ever claims ready
+// blocks, so no CTA holds an SM while it waits for a dependency.
+
+constexpr int kIsolated = -2;  // height_of_mb of a lost block with no lost neighbour
+
+__device__ __forceinline__ int bucket_key(const WorkDev& W, int h) {
+    return h == kIsolated ? W.nbk - 1 : max(0, W.nbk - 2 - h);
+}
 
 struct SegFV {
     int f;  // a segment starts inside the combined range
@@ -2746,6 +2758,16 @@ __global__ void __launch_bounds__(kThreads) queue_heights_kernel(WorkDev W, int 
             const int xm = x0 + tid, x = F.mbw - 1 - xm;
             const bool in = xm < F.mbw;
             const bool lost = in && F.lost[y * F.mbw + x] != 0;
+            bool isolated = lost;
+            if (lost) {
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int yy = y + dy, xx = x + dx;
+                        if ((dy || dx) && yy >= 0 && yy < F.mbh && xx >= 0 && xx < F.mbw &&
+                            F.lost[yy * F.mbw + xx])
+                            isolated = false;
+                    }
+            }
             int down = 0;
             if (lost && support && y + 1 < F.mbh) {
                 for (int dx = -1; dx <= 1; ++dx) {
@@ -2769,8 +2791,9 @@ __global__ void __launch_bounds__(kThreads) queue_heights_kernel(WorkDev W, int 
                     atomicExch(&W.counters[2], 7);
                     h = min(max(h, 0), W.nbk - 1);
                 }
+                if (isolated) h = kIsolated;  // (height 0: nothing depends on it)
                 hgt[y * F.mbw + x] = h;
-                atomicAdd(&W.bk_off[W.nbk - 1 - h], 1);
+                atomicAdd(&W.bk_off[bucket_key(W, h)], 1);
                 ++cnt;
             } else if (in) {
                 hgt[y * F.mbw + x] = -1;
@@ -2822,7 +2845,7 @@ __global__ void __launch_bounds__(kThreads) queue_fill_kernel(WorkDev W, int sup
         const int rank = block_exscan(lost, scan, &tot) + run;
         if (i < nmb) {
             if (lost) {
-                const int key = W.nbk - 1 - W.height_of_mb[F.mb_base + i];
+                const int key = bucket_key(W, W.height_of_mb[F.mb_base + i]);
                 const int e = W.bk_off[key] + atomicAdd(&W.bk_cnt[key], 1);
                 W.entry_of_mb[F.mb_base + i] = e;
                 W.entries[e] = make_int4(f, i, rank, key);

@@ -90,6 +90,12 @@ def test_constant_and_fully_lost(gpu_ctx):
     m = np.ones((2, 3), np.uint8)
     g = skmmse.conceal_numpy(f, m, skmmse.params("efficient"), ctx=gpu_ctx)
     assert np.all(g["out"] == 128)
+    # one row of blocks, all lost: a chain through every block of the frame (the longest
+    # chain a frame can hold, the top work-queue bucket)
+    f = synth.make_frame(80, 16, 3)
+    m = np.ones((1, 5), np.uint8)
+    g = skmmse.conceal_numpy(f, m, skmmse.params("efficient"), ctx=gpu_ctx)
+    assert np.all(g["out"] == 128)
 
 
 def test_batch_equals_single_calls(gpu_ctx):

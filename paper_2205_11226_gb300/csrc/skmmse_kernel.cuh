@@ -453,37 +453,39 @@ struct CtxStats {
 };
 
 // context of the window at (wr, wc): size, flatness and mean.  Warp-level reductions; every
-// lane returns the same values.  Support values lie in [0, 255] (clipped estimates, 8-bit
-// pixels), where the order of the FP32 bit patterns (with -0 folded to +0) is the order of
-// the values: the maximum and minimum are single integer warp reductions.
+// lane returns the same values.  Lane l takes window position l (raster order) and lanes
+// 0..3 also position 32 + l; both positions' availability rows and values are read at once
+// (the values unconditionally: they lie inside the region).  Support values lie in
+// [0, 255] (clipped estimates, 8-bit pixels), where the order of the FP32 bit patterns
+// (with -0 folded to +0) is the order of the values: the maximum and minimum are single
+// integer warp reductions.  The sum adds each lane's one or two values, then a butterfly
+// over the lanes: a fixed order of FP32 additions.
 __device__ __forceinline__ CtxStats ctx_stats(const Smem& sm, int wr, int wc, int lane) {
-    unsigned mxb = 0u, mnb = 0xFFFFFFFFu;
-    float sum = 0.0f;
-    unsigned bal[2];
-#pragma unroll
-    for (int h2 = 0; h2 < 2; ++h2) {  // window position k of this lane: its availability bit
-        const int k = lane + 32 * h2;
-        const int r = k / 6, c = k - 6 * (k / 6);
-        const bool own = (r == 2 || r == 3) && (c == 2 || c == 3);  // the patch: never context
-        const bool on = k < 36 && !own && ((sm.av[wr + r] >> (wc + c)) & 1ull);
-        bal[h2] = __ballot_sync(0xffffffffu, on);
-        if (on) {
-            const float v = sm.S[(wr + r) * kReg + wc + c];
-            const unsigned b = __float_as_uint(v + 0.0f);  // -0 -> +0
-            mxb = max(mxb, b);
-            mnb = min(mnb, b);
-            sum += v;
-        }
+    const int r0 = lane / 6, c0 = lane - 6 * (lane / 6);  // position lane (rows 0..5)
+    const int c1 = 2 + (lane & 3);                        // position 32 + lane: row 5
+    const bool own = (r0 == 2 || r0 == 3) && (c0 == 2 || c0 == 3);  // the patch: never context
+    const unsigned long long row0 = sm.av[wr + r0], row1 = sm.av[wr + 5];
+    const float v0 = sm.S[(wr + r0) * kReg + wc + c0];
+    const float v1 = sm.S[(wr + 5) * kReg + wc + c1];
+    const bool on0 = !own && ((row0 >> (wc + c0)) & 1ull);
+    const bool on1 = lane < 4 && ((row1 >> (wc + c1)) & 1ull);
+    const unsigned b0 = __float_as_uint(v0 + 0.0f), b1 = __float_as_uint(v1 + 0.0f);  // -0 -> +0
+    unsigned mxb = on0 ? b0 : 0u, mnb = on0 ? b0 : 0xFFFFFFFFu;
+    if (on1) {
+        mxb = max(mxb, b1);
+        mnb = min(mnb, b1);
     }
-    const unsigned long long ymask = (unsigned long long)bal[0] | ((unsigned long long)bal[1] << 32);
+    float sum = on0 ? 0.0f + v0 : 0.0f;
+    if (on1) sum += v1;
+    const int ny = __popc(__ballot_sync(0xffffffffu, on0)) + __popc(__ballot_sync(0xffffffffu, on1));
     mxb = __reduce_max_sync(0xffffffffu, mxb);
     mnb = __reduce_min_sync(0xffffffffu, mnb);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     CtxStats cs;
-    cs.ny = __popcll(ymask);
-    cs.phi = cs.ny > 0 ? __uint_as_float(mxb) - __uint_as_float(mnb) : 0.0f;
-    cs.mean = cs.ny > 0 ? sum / (float)cs.ny : 0.0f;
+    cs.ny = ny;
+    cs.phi = ny > 0 ? __uint_as_float(mxb) - __uint_as_float(mnb) : 0.0f;
+    cs.mean = ny > 0 ? sum / (float)ny : 0.0f;
     return cs;
 }
 
@@ -2228,12 +2230,12 @@ __device__ __noinline__ int claim_ready(const WorkDev& W, int n_entries, unsigne
     int seen = -1;
     for (;;) {
         const int claimed = ld_relaxed_i(&W.counters[1]);
+        const int k0 = ld_relaxed_i(&W.counters[3]);  // (issued before the test: one round trip)
         if (claimed >= n_entries) return -1;
         if (claimed != seen) {
             seen = claimed;
             idle = 0;
         }
-        const int k0 = ld_relaxed_i(&W.counters[3]);
         bool lost_race = false;
         for (int kb = k0; kb < W.nbk; kb += 32) {
             const int k = kb + lane;
@@ -2252,7 +2254,19 @@ __device__ __noinline__ int claim_ready(const WorkDev& W, int n_entries, unsigne
             if (ready) {
                 const int src = __ffs(ready) - 1;
                 int pos = -1;
-                if (lane == src && atomicCAS(&W.bk_head[k], hd, hd + 1) == hd) pos = W.bk_off[k] + hd;
+                if (lane == src) {
+                    // a lost race returns the head another claimer left: while it is still
+                    // below the tail seen (the tail only grows), try again on the same bucket
+                    int h = hd;
+                    for (int t = 0; t < 64 && h < tl; ++t) {
+                        const int old = atomicCAS(&W.bk_head[k], h, h + 1);
+                        if (old == h) {
+                            pos = W.bk_off[k] + h;
+                            break;
+                        }
+                        h = old;
+                    }
+                }
                 pos = __shfl_sync(0xffffffffu, pos, src);
                 if (pos < 0) {
                     lost_race = true;
@@ -2453,29 +2467,35 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
             // back; it stops at the first step that needs IDL and hands it to the CTA.
             if (wid == 0) {
                 long long n_brl = 0, n_empty = 0, flops = 0, sum_ny = 0;
+                int p = step < npatch ? sm.order[step] : 0;
                 for (; step < npatch; ++step) {
-                    const int p = sm.order[step];
+                    // (the next patch of the order, read ahead of this step's chain of loads)
+                    const int p_next = step + 1 < npatch ? sm.order[step + 1] : 0;
                     const int pa = p >> 3, pb = p & 7;
                     const int wr = kMB + 2 * pa - 2, wc = kMB + 2 * pb - 2;
+                    const int pr = wr + 2, pc = wc + 2;
+                    // lanes 0..3: pixel (lane >> 1, lane & 1) of the patch, its availability row
+                    const unsigned long long prow = sm.av[pr + ((lane >> 1) & 1)];
                     const CtxStats cs = ctx_stats(sm, wr, wc, lane);
-                    if (lane == 0) {
-                        sm.hand.pa = pa;
-                        sm.hand.pb = pb;
-                        sm.hand.ny = cs.ny;
-                        sm.hand.phi = cs.phi;
-                        sm.hand.mean = cs.mean;
-                    }
                     SK_PHASE(PH_CTX);
-                    if (cs.ny > 0 && cs.phi > P.t_phi) break;
+                    if (cs.ny > 0 && cs.phi > P.t_phi) {  // hand the step to the CTA
+                        if (lane == 0) {
+                            sm.hand.pa = pa;
+                            sm.hand.pb = pb;
+                            sm.hand.ny = cs.ny;
+                            sm.hand.phi = cs.phi;
+                            sm.hand.mean = cs.mean;
+                        }
+                        break;
+                    }
                     const float xv = cs.ny == 0 ? 128.0f : cs.mean;
                     const int layer = cs.ny == 0 ? L_EMPTY : L_BRL;
-                    const int pr = wr + 2, pc = wc + 2;
                     if (lane < 4) {
                         float xw = fminf(fmaxf(xv, 0.0f), 255.0f);
                         if (force_on && trace_base) xw = trace_base[step].x[lane];  // verification hook
                         if (quant_on) xw = rintf(xw);
                         const int rr = pr + (lane >> 1), cc = pc + (lane & 1);
-                        if (!((sm.av[rr] >> cc) & 1ull)) sm.S[rr * kReg + cc] = xw;  // lost pixels only
+                        if (!((prow >> cc) & 1ull)) sm.S[rr * kReg + cc] = xw;  // lost pixels only
                     }
                     __syncwarp();
                     if (lane == 0) {
@@ -2508,6 +2528,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                     }
                     __syncwarp();
                     SK_PHASE(PH_BRL);
+                    p = p_next;
                 }
                 if (lane == 0) {
                     sm.hand.step = step;

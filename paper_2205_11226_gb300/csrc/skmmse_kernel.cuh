@@ -978,6 +978,10 @@ __device__ __forceinline__ bool stage_zt(Smem& sm, int c0, int n, int nz, float 
         if (ri >= nr) continue;
         const int a = ri < nz ? ri : 36;
         const int ka = a < kZs ? h.koff[a] : -1;
+        // the group's 8 candidate indices in one 16-byte load (c0 + 8 g8 is a multiple of 8;
+        // h.cand holds 7 entries past the last candidate, so a group past M reads inside it)
+        const uint4 cq = *reinterpret_cast<const uint4*>(&h.cand[c0 + 8 * g8]);
+        const uint32_t cw[4] = {cq.x, cq.y, cq.z, cq.w};
         float v[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
@@ -985,7 +989,7 @@ __device__ __forceinline__ bool stage_zt(Smem& sm, int c0, int n, int nz, float 
             float x = 0.0f;
             if (j < n) {
                 if (a == 36) x = 1.0f;
-                else if (ka >= 0) x = sm.S[h.cand[c0 + j] + ka] - shift;
+                else if (ka >= 0) x = sm.S[(int)((cw[t >> 1] >> (16 * (t & 1))) & 0xFFFFu) + ka] - shift;
             }
             v[t] = x;
         }
@@ -1162,10 +1166,18 @@ __device__ __noinline__ float h2_mixed(int M, int ny, float shift, uint32_t tmem
             const int j = (q & 7) | ((q >> gsh) << 3), l8 = (q >> 3) & (G - 1);
             float v[8];
             const int base = j < n ? h.cand[c0 + j] : 0;
+            // the 8 context offsets and centred context values of column group l8 in 16-byte
+            // loads (l8 < 4: inside the 36-entry lists)
+            const uint4 oq = *reinterpret_cast<const uint4*>(&h.off[8 * l8]);
+            const float4 y0v = *reinterpret_cast<const float4*>(&h.ys[8 * l8]);
+            const float4 y1v = *reinterpret_cast<const float4*>(&h.ys[8 * l8 + 4]);
+            const uint32_t ow[4] = {oq.x, oq.y, oq.z, oq.w};
+            const float yv[8] = {y0v.x, y0v.y, y0v.z, y0v.w, y1v.x, y1v.y, y1v.z, y1v.w};
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
                 const int l = 8 * l8 + t;
-                v[t] = (j < n && l < ny) ? (sm.S[base + h.off[l]] - shift) - h.ys[l] : 0.0f;
+                const int o = (int)(short)((ow[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
+                v[t] = (j < n && l < ny) ? (sm.S[base + o] - shift) - yv[t] : 0.0f;
             }
             store8_split<BF16, true>(tile(h, o), tile(h, o + L::kA), j, 8 * l8, KH, v);
         }
@@ -1256,10 +1268,15 @@ __device__ __noinline__ void h3_mixed(const KParams& P, int M, int nz, float shi
             if (b < nb) {
                 float v[8];
                 const float ib = P.inv2beta[b];
+                // the group's 8 distances in two 16-byte loads (h.d holds 7 entries past the
+                // last candidate)
+                const float4 d0 = *reinterpret_cast<const float4*>(&h.d[c0 + 8 * g8]);
+                const float4 d1 = *reinterpret_cast<const float4*>(&h.d[c0 + 8 * g8 + 4]);
+                const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                     const int j = 8 * g8 + t;
-                    v[t] = j < n ? __expf(-(h.d[c0 + j] - dmin) * ib) : 0.0f;
+                    v[t] = j < n ? __expf(-(dv[t] - dmin) * ib) : 0.0f;
                 }
                 store8_split<BF16>(wt(bf, 0), wt(bf, 1), b, 8 * g8, 64, v);
             }
@@ -2901,6 +2918,8 @@ namespace sk {
 static_assert(sizeof(Smem) <= 113 * 1024, "two CTAs per SM");
 static_assert(offsetof(Hql, mx) % 16 == 0 && sizeof(Hql::mx) == 4 * 128 * 64 * 2, "tensor-core tiles");
 static_assert((offsetof(Smem, hql) + offsetof(Hql, mx)) % 128 == 0, "tensor-core tiles on 128-byte lines");
+static_assert(offsetof(Hql, cand) % 16 == 0 && offsetof(Hql, d) % 16 == 0 && offsetof(Hql, off) % 16 == 0,
+              "16-byte loads of candidate indices, distances and context offsets");
 static_assert(offsetof(Hql, Z) % 16 == 0 && offsetof(Hql, Linv) % 16 == 0 && offsetof(Hql, G) % 16 == 0 &&
                   offsetof(Hql, ys) % 16 == 0 && offsetof(Smem, hql) % 16 == 0,
               "float4 operands");

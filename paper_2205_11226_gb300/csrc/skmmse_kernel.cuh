@@ -2425,51 +2425,72 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
         }
         phase ^= (F.use_tma ? 1u : 0u);
         __syncthreads();
-        // convert to values + availability (ballot per row half)
-        for (int r = wid; r < kReg; r += kWarps) {
-            unsigned long long bits = 0;
+        // convert to values + availability (ballot per row half).  A warp takes rows wid,
+        // wid + 8, ..., every value of its 6 rows read (the dependencies' values from L2)
+        // before any is stored.
+        {
+            constexpr int kRows = kReg / kWarps;
+            float v[kRows][2];
+            bool av[kRows][2];
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int cc = half * 32 + lane;
-                bool av = false;
-                float v = 0.0f;
-                if (cc < kReg) {
-                    const int fy = oy + r, fx = ox + cc;
-                    if (fy >= 0 && fx >= 0 && fy < F.h && fx < F.w) {
-                        const int nb = (r / kMB) * 3 + cc / kMB;
-                        const int st = sm.nbst[nb];
-                        if (st == 0) {
-                            v = F.use_tma ? (float)sm.raw[r * kReg + cc]
-                                          : (float)F.in[(size_t)fy * F.pitch + fx];
-                            av = true;
-                        } else if (st == 1) {
-                            v = __ldcg(&W.vals[(size_t)sm.nbent[nb] * 256 + (r % kMB) * kMB + cc % kMB]);
-                            av = true;
-                        } else if (F.px_lost && F.px_lost[(size_t)fy * F.px_pitch + fx] == 0) {
-                            // a received pixel of a lost block (per-pixel loss)
-                            v = F.use_tma ? (float)sm.raw[r * kReg + cc]
-                                          : (float)F.in[(size_t)fy * F.pitch + fx];
-                            av = true;
+            for (int q = 0; q < kRows; ++q) {
+                const int r = wid + kWarps * q;
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const int cc = half * 32 + lane;
+                    bool a = false;
+                    float x = 0.0f;
+                    if (cc < kReg) {
+                        const int fy = oy + r, fx = ox + cc;
+                        if (fy >= 0 && fx >= 0 && fy < F.h && fx < F.w) {
+                            const int nb = (r / kMB) * 3 + cc / kMB;
+                            const int st = sm.nbst[nb];
+                            if (st == 0) {
+                                x = F.use_tma ? (float)sm.raw[r * kReg + cc]
+                                              : (float)F.in[(size_t)fy * F.pitch + fx];
+                                a = true;
+                            } else if (st == 1) {
+                                x = __ldcg(&W.vals[(size_t)sm.nbent[nb] * 256 + (r % kMB) * kMB + cc % kMB]);
+                                a = true;
+                            } else if (F.px_lost && F.px_lost[(size_t)fy * F.px_pitch + fx] == 0) {
+                                // a received pixel of a lost block (per-pixel loss)
+                                x = F.use_tma ? (float)sm.raw[r * kReg + cc]
+                                              : (float)F.in[(size_t)fy * F.pitch + fx];
+                                a = true;
+                            }
                         }
                     }
-                    sm.S[r * kReg + cc] = v;
+                    v[q][half] = x;
+                    av[q][half] = a;
                 }
-                const unsigned bal = __ballot_sync(0xffffffffu, av);
-                bits |= (unsigned long long)bal << (32 * half);
             }
-            if (lane == 0) sm.av[r] = bits;
+#pragma unroll
+            for (int q = 0; q < kRows; ++q) {
+                const int r = wid + kWarps * q;
+                unsigned long long bits = 0;
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const int cc = half * 32 + lane;
+                    if (cc < kReg) sm.S[r * kReg + cc] = v[q][half];
+                    bits |= (unsigned long long)__ballot_sync(0xffffffffu, av[q][half]) << (32 * half);
+                }
+                if (lane == 0) sm.av[r] = bits;
+            }
         }
         __syncthreads();
-        if (tid == 0) {  // patches to fill: in the frame, holding a lost (unavailable) pixel
-            unsigned long long uf = 0;
-            for (int a = 0; a < 8; ++a)
-                for (int b = 0; b < 8; ++b) {
-                    const int pr = kMB + 2 * a, pc = kMB + 2 * b;
-                    const bool full = ((sm.av[pr] >> pc) & 3ull) == 3ull && ((sm.av[pr + 1] >> pc) & 3ull) == 3ull;
-                    if (mby * kMB + 2 * a < F.h && mbx * kMB + 2 * b < F.w && !full) uf |= 1ull << (a * 8 + b);
-                }
-            sm.unfilled = uf;
-            sm.st[ST_LOST] += 1;
+        if (wid == 0) {  // patches to fill: in the frame, holding a lost (unavailable) pixel
+            unsigned bal[2];
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {  // lane l: patches l and l + 32
+                const int p = lane + 32 * h2, a = p >> 3, b = p & 7;
+                const int pr = kMB + 2 * a, pc = kMB + 2 * b;
+                const bool full = ((sm.av[pr] >> pc) & 3ull) == 3ull && ((sm.av[pr + 1] >> pc) & 3ull) == 3ull;
+                bal[h2] = __ballot_sync(0xffffffffu, mby * kMB + 2 * a < F.h && mbx * kMB + 2 * b < F.w && !full);
+            }
+            if (lane == 0) {
+                sm.unfilled = (unsigned long long)bal[0] | ((unsigned long long)bal[1] << 32);
+                sm.st[ST_LOST] += 1;
+            }
         }
         __syncthreads();
 
@@ -2918,6 +2939,7 @@ namespace sk {
 static_assert(sizeof(Smem) <= 113 * 1024, "two CTAs per SM");
 static_assert(offsetof(Hql, mx) % 16 == 0 && sizeof(Hql::mx) == 4 * 128 * 64 * 2, "tensor-core tiles");
 static_assert((offsetof(Smem, hql) + offsetof(Hql, mx)) % 128 == 0, "tensor-core tiles on 128-byte lines");
+static_assert(kReg % kWarps == 0, "rows of the support region per warp");
 static_assert(offsetof(Hql, cand) % 16 == 0 && offsetof(Hql, d) % 16 == 0 && offsetof(Hql, off) % 16 == 0,
               "16-byte loads of candidate indices, distances and context offsets");
 static_assert(offsetof(Hql, Z) % 16 == 0 && offsetof(Hql, Linv) % 16 == 0 && offsetof(Hql, G) % 16 == 0 &&

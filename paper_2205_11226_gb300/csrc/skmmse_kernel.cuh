@@ -237,6 +237,7 @@ struct __align__(128) Smem {
     int entry;
     int pad0;
     struct {
+        unsigned long long ymask;
         int step, pa, pb, ny;
         float phi, mean;
     } hand;                            // step handed from warp 0 to the CTA
@@ -383,26 +384,26 @@ struct StepCtx {
     float y0w[36];       // window values (0 where unavailable)
 };
 
-// candidate window (u, v) valid: every configured position available
+// candidate window (u, v) valid: every configured position available (the six rows read
+// at once, no early exit)
 __device__ __forceinline__ bool cand_valid(const Smem& sm, const StepCtx& c, int u, int v) {
-    bool ok = true;
+    unsigned missing = 0u;
 #pragma unroll
-    for (int r = 0; r < 6; ++r) {
-        const unsigned bits = (unsigned)(sm.av[u + r] >> v) & 63u;
-        ok = ok && ((c.rowcfg[r] & ~bits) == 0u);
-    }
-    return ok;
+    for (int r = 0; r < 6; ++r) missing |= c.rowcfg[r] & ~((unsigned)(sm.av[u + r] >> v) & 63u);
+    return missing == 0u;
 }
 
-// squared Euclidean context distance of window (base = u*48+v), Eq. (15)
+// squared Euclidean context distance of window (base = u*48+v), Eq. (15).  All 36 window
+// values are read (the window lies inside the region); a position outside the context adds
+// fma(0, 0, d) = d exactly (the partial sums are never -0), so the sums are those of the
+// context positions alone, without a branch per position.
 __device__ __forceinline__ float ctx_dist(const float* S, const StepCtx& c, int base) {
     float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // four partial sums: independent FMA chains
 #pragma unroll
     for (int k = 0; k < 36; ++k) {
-        if ((c.ymask >> k) & 1ull) {
-            const float t = c.y0w[k] - S[base + (k / 6) * kReg + (k % 6)];
-            d[k & 3] = __fmaf_rn(t, t, d[k & 3]);
-        }
+        const float diff = c.y0w[k] - S[base + (k / 6) * kReg + (k % 6)];
+        const float t = ((c.ymask >> k) & 1ull) ? diff : 0.0f;
+        d[k & 3] = __fmaf_rn(t, t, d[k & 3]);
     }
     return (d[0] + d[1]) + (d[2] + d[3]);
 }
@@ -448,6 +449,7 @@ constexpr float kNegBig = -1.0e30f;
 // IDL: Eq. (15) over growing rings; returns 1 accepted, 0 not accepted, -1 no candidate
 
 struct CtxStats {
+    unsigned long long ymask;  // context positions, window raster order (the patch excluded)
     int ny;
     float phi, mean;  // flatness (max - min) and mean of the context, Eqs. (16)-(17)
 };
@@ -477,12 +479,14 @@ __device__ __forceinline__ CtxStats ctx_stats(const Smem& sm, int wr, int wc, in
     }
     float sum = on0 ? 0.0f + v0 : 0.0f;
     if (on1) sum += v1;
-    const int ny = __popc(__ballot_sync(0xffffffffu, on0)) + __popc(__ballot_sync(0xffffffffu, on1));
+    const unsigned bal0 = __ballot_sync(0xffffffffu, on0), bal1 = __ballot_sync(0xffffffffu, on1);
+    const int ny = __popc(bal0) + __popc(bal1);
     mxb = __reduce_max_sync(0xffffffffu, mxb);
     mnb = __reduce_min_sync(0xffffffffu, mnb);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     CtxStats cs;
+    cs.ymask = (unsigned long long)bal0 | ((unsigned long long)bal1 << 32);
     cs.ny = ny;
     cs.phi = ny > 0 ? __uint_as_float(mxb) - __uint_as_float(mnb) : 0.0f;
     cs.mean = ny > 0 ? sum / (float)ny : 0.0f;
@@ -2518,6 +2522,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
                     SK_PHASE(PH_CTX);
                     if (cs.ny > 0 && cs.phi > P.t_phi) {  // hand the step to the CTA
                         if (lane == 0) {
+                            sm.hand.ymask = cs.ymask;
                             sm.hand.pa = pa;
                             sm.hand.pb = pb;
                             sm.hand.ny = cs.ny;
@@ -2586,12 +2591,7 @@ __global__ void __launch_bounds__(kThreads, 2) conceal_kernel(const __grid_const
             c.pb = sm.hand.pb;
             c.wr = kMB + 2 * c.pa - 2;
             c.wc = kMB + 2 * c.pb - 2;
-            c.ymask = 0;
-#pragma unroll
-            for (int r = 0; r < 6; ++r) {  // context: the window less the patch
-                const unsigned bits = (unsigned)(sm.av[c.wr + r] >> c.wc) & ((r == 2 || r == 3) ? 0x33u : 63u);
-                c.ymask |= (unsigned long long)bits << (6 * r);
-            }
+            c.ymask = sm.hand.ymask;  // context: the window less the patch (from warp 0's ballots)
             c.ny = sm.hand.ny;
             c.phi = sm.hand.phi;
             c.mean = sm.hand.mean;

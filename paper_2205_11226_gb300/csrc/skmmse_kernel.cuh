@@ -427,14 +427,16 @@ __device__ __forceinline__ void annulus_pos(int i, int rin, int rout, int* dy, i
     }
 }
 
+// (the rescale as a select: the factor is exactly 1 unless s is a new maximum; its products
+// rounded on their own, as in the branch form)
 __device__ __forceinline__ void online_add(float s, float x0, float x1, float x2, float x3,
                                            float& m, float& s0, float sx[4]) {
-    if (s > m) {
-        const float sc = __expf(m - s);
-        s0 *= sc;
-        sx[0] *= sc; sx[1] *= sc; sx[2] *= sc; sx[3] *= sc;
-        m = s;
-    }
+    const float e = __expf(m - s);
+    const float sc = s > m ? e : 1.0f;
+    s0 = __fmul_rn(s0, sc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sx[q] = __fmul_rn(sx[q], sc);
+    m = fmaxf(m, s);
     const float w = __expf(s - m);
     s0 += w;
     sx[0] = __fmaf_rn(w, x0, sx[0]);
@@ -1441,14 +1443,17 @@ __device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
 }
 
 // one step of a max-subtracted online softmax sum: score sc, values [x' | G u]
+// The rescale is a select, not a branch (the lanes are different members and diverge): the
+// factor is exp(m - sc) for a new maximum (0 when m = -inf) and exactly 1 otherwise.  Its
+// products are rounded on their own (__fmul_rn: not fused with the additions that follow),
+// so the sums are those of the branch bit for bit.
 __device__ __forceinline__ void h5_online(float sc, float4 xv, float4 gv, float& m, float& sw, float sa[8]) {
-    if (sc > m) {
-        const float r = __expf(m - sc);  // 0 when m = -inf
-        sw *= r;
+    const float e = __expf(m - sc);
+    const float r = sc > m ? e : 1.0f;
+    sw = __fmul_rn(sw, r);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) sa[k] *= r;
-        m = sc;
-    }
+    for (int k = 0; k < 8; ++k) sa[k] = __fmul_rn(sa[k], r);
+    m = fmaxf(m, sc);
     const float w = __expf(sc - m);
     sw += w;
     sa[0] = __fmaf_rn(w, xv.x, sa[0]);

@@ -39,6 +39,9 @@ sys.path.insert(0, ROOT)
 METRIC = "concealed 16x16 MBs/s and 1080p frames/s on 1 GB300, mixed vs FP32, at \u22640.01 dB PSNR delta"
 UNIT = "MB/s"
 WORKLOAD = "batch64_mixed_24x352x288_24x1280x720_16x1920x1080_loss5-30pct"
+# DRAM bytes per launch of the concealment kernel on the 64-frame batch, FP16, launch
+# configuration (2, 64, 128), from one ncu capture (205.8 MB read + 321.1 MB written)
+CAPTURED_TRAFFIC_BYTES = 526_887_424
 FP32_LANES_PER_SM = 128  # FP32 lanes of one sm_103a SM (4 partitions x 32)
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
 DTYPES = {"fp32": "f32", "bf16": "bf16+f32", "fp16": "f16+f32"}
@@ -572,8 +575,15 @@ def run_ours(args):
     if not max_mhz:  # no clock samples: the device's maximum SM clock as the driver reports it
         max_mhz = query_max_sm_mhz(local)
     peak = n_sm * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    # DRAM bytes of one concealment launch (dram__bytes_read.sum + dram__bytes_write.sum of an
+    # ncu capture of this kernel at this workload, precision and launch configuration:
+    # profiles/conceal_kernel_batch64_fp16.md); other settings have no capture
+    cfg_now = ctx.get_config(fd, md, p)
+    traffic = (CAPTURED_TRAFFIC_BYTES if (args.workload == "batch" and args.precision == "fp16" and
+                                          (cfg_now["ctas_per_sm"], cfg_now["tile_cov"], cfg_now["tile_dist"])
+                                          == (2, 64, 128)) else None)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"FP32 FMA: {n_sm} SMs (device) x {FP32_LANES_PER_SM} lanes x 2 FLOP x "
                                f"{max_mhz:.0f} MHz (sampled maximum SM clock); derived",
                 "alg_flops_per_step": flops}

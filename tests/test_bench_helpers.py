@@ -75,3 +75,19 @@ def test_lost_blocks_counts_block_and_pixel_masks():
     px = synth.lost_pixel_mask(m, 64, 48)
     px[20, 5] = 1  # one more block, (1, 0), holds a lost pixel
     assert bench.lost_blocks(f, px) == 3
+
+
+def test_packed_views_layout():
+    # the bench's arenas: every array at a 256-byte aligned offset, the views holding the data
+    import torch
+    arrays = [np.arange(35, dtype=np.uint8).reshape(5, 7), np.full((3, 4), 9, np.uint8),
+              np.arange(600, dtype=np.uint16).astype(np.uint8).reshape(20, 30)]
+    n = bench.packed_size(arrays)
+    assert n == 512 + 600
+    buf = torch.zeros(n, dtype=torch.uint8)
+    views = bench.packed_views(arrays, buf)
+    for v, a in zip(views, arrays):
+        assert v.data_ptr() % 256 == buf.data_ptr() % 256
+        v.numpy()[...] = a
+    for v, a in zip(bench.packed_views(arrays, buf), arrays):
+        assert np.array_equal(v.numpy(), a)
